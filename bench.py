@@ -1,0 +1,339 @@
+"""Benchmark of the FMM self-gravity solve on GB300 (one JSON line on stdout).
+
+Metric: cell-interactions/s = (ordered same-level M2L + cross-level M2L +
+same-level P2P + cross-level P2P interactions of one solve) / time of one solve.
+A step is one full solve (P2M, M2M, M2L + correction, cross-level, P2P, L2L,
+L2P) over the synthetic input, replayed from the library's CUDA graph.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--precision mixed|fp64] [--impl ours|reference]
+
+Default workload: adaptive7 (7-level adaptive octree of a q=0.7 binary of n=1.5
+polytropes, ~8000 leaf subgrids of 8^3 cells), mixed precision, with the float64
+path timed beside it.  N > 1 runs one independent replica per GPU (the solve
+needs no exchange between GPUs); `value` sums the replicas' work over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-interactions/s"
+L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
+
+# Peaks for the roofline (per GPU, at the 2070 MHz maximum SM clock of the recipe):
+#  float64: 1.25 TFLOP/s nominal -> 4 flop / clock / SM = 152 * 4 * 2.07e9
+#  float32: 128 lanes x 2 flop / clock / SM -> 152 * 256 * 2.07e9
+PEAK_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+PEAK_FP32_TFLOPS = 152 * 256 * 2.07e9 / 1e12
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(w, seconds_target: float = 15.0, theta: float = 0.5):
+    """The oracle as it stands on the host cores, over a seeded sample of leaf cells
+    (the oracle evaluates the sample's interaction lists and those of its ancestors)."""
+    import oracle
+    nl = w.tree.n_leaf * 512
+    rng = np.random.default_rng(123)
+    n_probe = 64
+    idx = rng.choice(nl, size=min(n_probe, nl), replace=False)
+    mask = np.zeros(nl, np.uint8)
+    mask[idx] = 1
+    work = np.zeros(1, np.int64)
+    t0 = time.perf_counter()
+    oracle.fmm(w.tree, w.rho, theta, leaf_mask=mask, work=work)
+    dt = time.perf_counter() - t0
+    # scale the sample to about seconds_target of CPU work
+    n = int(min(nl, max(n_probe, n_probe * seconds_target / max(dt, 1e-3))))
+    idx = rng.choice(nl, size=n, replace=False)
+    mask[:] = 0
+    mask[idx] = 1
+    t0 = time.perf_counter()
+    oracle.fmm(w.tree, w.rho, theta, leaf_mask=mask, work=work)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": float(work[0]) / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {nl} leaf cells of {w.name} (their and their ancestors' interaction lists, "
+                      f"{int(work[0])} interactions, {dt:.1f} s, including the full upward pass)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    from paper_2304_11002_gb300 import workloads as W
+    w = W.make(args.workload)
+    import oracle
+    oracle.lib()
+    per_step = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, seconds_target=args.ref_seconds)
+        if i >= args.warmup:
+            per_step.append(cb["value"])
+    value = float(np.mean(per_step))
+    ms = 1e3 * counts_total(w) / value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "note": w.note, "theta": w.theta, "order": 3},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+_COUNTS_CACHE = {}
+
+
+def counts_total(w):
+    from paper_2304_11002_gb300 import binding
+    key = id(w)
+    if key not in _COUNTS_CACHE:
+        _COUNTS_CACHE[key] = int(binding.octo_fmm_plan_counts(w.tree, w.theta).sum())
+    return _COUNTS_CACHE[key]
+
+
+def time_solver(w, precision, steps, warmup, torch, flush, stream):
+    from paper_2304_11002_gb300 import binding
+    fmm = binding.OctoFMM(w.tree, w.theta, precision)
+    h = fmm.handle
+    binding.octo_fmm_set_option(h, 2, 1)  # stage events inside the captured graph
+    nst = binding.octo_fmm_stage_count(h)
+    info = [binding.octo_fmm_stage_info(h, i) for i in range(nst)]
+    rho = torch.from_numpy(np.ascontiguousarray(w.rho.reshape(-1))).cuda()
+    phi = torch.empty(fmm.n_leaf_cells, dtype=torch.float64, device="cuda")
+    g = torch.empty((3, fmm.n_leaf_cells), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fmm.forces(rho, phi, g, stream)
+        stream.synchronize()
+        step_ms, stage_ms = [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(steps):
+            flush.zero_()  # evict L2 (outside the timed events)
+            e0.record(stream)
+            fmm.forces(rho, phi, g, stream)
+            e1.record(stream)
+            stream.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            stage_ms.append(binding.octo_fmm_stage_times(h))
+    launches = binding.octo_fmm_launches_per_solve(h)
+    return fmm, info, np.array(step_ms), np.array(stage_ms), launches, (rho, phi, g)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2304_11002_gb300 import binding, build
+    from paper_2304_11002_gb300 import workloads as W
+    build.build()
+    w = W.make(args.workload)
+    n_inter = counts_total(w)
+    counts = binding.octo_fmm_plan_counts(w.tree, w.theta)
+    precision = binding.OCTO_MIXED if args.precision == "mixed" else binding.OCTO_FP64
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        fmm, info, step_ms, stage_ms, launches, bufs = time_solver(w, precision, args.steps, args.warmup, torch,
+                                                                   flush, stream)
+    barrier()
+    t_step = float(np.mean(step_ms))
+    t_total = float(np.sum(step_ms)) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = n_inter * args.steps * ws / t_total
+
+    # dominant kernel of the step and its roofline
+    mean_stage = stage_ms.mean(axis=0)
+    k = int(np.argmax(mean_stage))
+    st = info[k]
+    dur_s = mean_stage[k] / 1e3
+    peaks = _measured_peaks()
+    if st["flops"] > 0:
+        fp32_stage = precision == binding.OCTO_MIXED and st["name"] in ("m2l_interior_f32", "leaf_m2l_f32")
+        peak = PEAK_FP32_TFLOPS if fp32_stage else PEAK_FP64_TFLOPS
+        achieved = st["flops"] / dur_s / 1e12
+        roof = {"bound": "alu", "kernel": st["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": ("derived: 152 SMs x %s x 2.07 GHz" % ("256 fp32 flop/clk" if fp32_stage else
+                                                                      "4 fp64 flop/clk (1.25 TFLOP/s nominal)"))}
+    else:
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        achieved = st["bytes"] / dur_s / 1e9
+        roof = {"bound": "hbm", "kernel": st["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": "measured" if peaks else "fallback"}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    nlc = fmm.n_leaf_cells
+    rho_h = np.ascontiguousarray(w.rho.reshape(-1))
+    phi_h = np.empty(nlc)
+    g_h = np.empty((3, nlc))
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            binding.octo_fmm_forces_host(fmm.handle, rho_h, phi_h, g_h, stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            binding.octo_fmm_forces_host(fmm.handle, rho_h, phi_h, g_h, stream)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+    e2e = {"value": n_inter * args.steps * ws / e2e_s, "unit": METRIC, "h2d_bytes_per_step": int(rho_h.nbytes),
+           "d2h_bytes_per_step": int(phi_h.nbytes + g_h.nbytes)}
+
+    # the float64 path on the same workload, for the mixed-vs-float64 comparison
+    fp64 = None
+    if precision == binding.OCTO_MIXED and not args.no_fp64:
+        del fmm
+        _, _, s_ms, _, _, _ = time_solver(w, binding.OCTO_FP64, max(2, args.steps // 2), 1, torch, flush, stream)
+        fp64 = {"value": n_inter / (float(np.mean(s_ms)) / 1e3), "ms_per_step": float(np.mean(s_ms))}
+
+    if rank != 0:
+        return 0
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if precision == binding.OCTO_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "note": w.note, "precision": args.precision, "theta": w.theta, "order": 3,
+                   "n_leaf_subgrids": int(w.tree.n_leaf), "n_nodes": int(w.tree.n_nodes),
+                   "interactions_per_step": n_inter,
+                   "counts": {"m2l_same": int(counts[0]), "m2l_cross": int(counts[1]), "p2p_same": int(counts[2]),
+                              "p2p_cross": int(counts[3])},
+                   "l2": "flushed before every timed step (256 MB write, outside the timed events)",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single GPU"},
+        "roofline": roof,
+        "stages_ms": {info[i]["name"]: round(float(mean_stage[i]), 4) for i in range(len(info))},
+        "e2e": e2e,
+        "gpu_launches": int(launches * args.steps),
+        "clocks": clocks,
+    }
+    if fp64 is not None:
+        line["fp64_path"] = fp64
+        line["mixed_over_fp64"] = value / ws / fp64["value"]
+    if not args.no_cpu_baseline and ws == 1:
+        cb = cpu_baseline(w, seconds_target=args.ref_seconds)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="adaptive7")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * octo_fmm.h -- C ABI of the GB300 (sm_103a) fast-multipole self-gravity solver.
+ *
+ * The method is the gravity solver of Octo-Tiger as described in the paper's
+ * Section IV-C ("Octo-Tiger"): an adaptive octree whose nodes are leaves or fully
+ * refined, each node carrying an 8x8x8 subgrid of cells; a leaf cell is a single
+ * monopole at the cell centre, interior cells carry monopole, quadrupole and
+ * octupole moments about their centre of mass; a modification conserves angular
+ * momentum.  The solve runs in the three phases of Section VII-C: a bottom-up
+ * traversal (P2M, M2M), same-level cell-to-cell interactions on each level (M2L,
+ * plus P2P between near leaf cells), and a top-down traversal (L2L, L2P).
+ * Units: G = 1, phi = -sum m / r, g = -grad phi.
+ *
+ * Conventions for every call below
+ *  - Pointers named *_dev are device pointers (cudaMalloc'd or torch CUDA memory)
+ *    owned by the caller; they must stay valid until the stream work completes.
+ *  - rho, phi: float64 [n_leaf * 512]; g: float64 [3][n_leaf * 512] (structure of
+ *    arrays).  Leaves are ordered as they appear in the descriptor's node array;
+ *    the 512 cells of a leaf are x-fastest (local = a + 8 b + 64 c).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute calls are
+ *    asynchronous: they enqueue work and return.  Launch and argument errors are
+ *    returned immediately; errors detected on the device (bounded waits that ran
+ *    out) are reported by the next call on the handle.
+ *  - Return value: OCTO_OK (0) or a negative OCTO_E* status; octo_fmm_last_error()
+ *    gives a message.  No C++ exception crosses this interface.
+ *  - One handle is not thread-safe; use one handle per host thread or serialise.
+ */
+#ifndef OCTO_FMM_H
+#define OCTO_FMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct octo_fmm* octo_fmm_t; /* opaque, owned by the library */
+
+/* Octree descriptor (host memory, owned by the caller, copied by create).
+ * Section IV-C: every node is a leaf or has all 8 children.
+ *  level[n]        level of node n, root = 0 (exactly one root)
+ *  ijk[n][3]       integer position of node n within its level, 0 <= ijk < 2^level
+ *  children[n][8]  child node by octant o = ox + 2 oy + 4 oz, or -1 (all -1 = leaf);
+ *                  child ijk = 2 ijk + (ox, oy, oz)
+ *  origin, extent  the cubic domain [origin, origin + extent)^3; cells of level l
+ *                  have width h_l = extent / (8 * 2^l). */
+typedef struct {
+  int32_t n_nodes;
+  const int32_t* level;
+  const int32_t* ijk;
+  const int32_t* children;
+  double origin[3];
+  double extent;
+} octo_tree_desc;
+
+enum {
+  OCTO_OK = 0,
+  OCTO_EINVAL = -1,   /* bad argument (null pointer, unsupported theta/order/precision) */
+  OCTO_ETREE = -2,    /* inconsistent octree descriptor */
+  OCTO_ENOMEM = -3,   /* device or host allocation failed */
+  OCTO_ECUDA = -4,    /* a CUDA runtime call failed */
+  OCTO_ETIMEOUT = -5, /* a bounded device-side wait ran out */
+  OCTO_ENONPOS = -6,  /* reserved: non-positive density reported by a check */
+  OCTO_ESTATE = -7    /* call out of order (e.g. backward before a forward solve) */
+};
+
+enum {
+  OCTO_FP64 = 0, /* every phase in IEEE float64 */
+  OCTO_MIXED = 1 /* far-field M2L in float32 with compensated sums; P2P, correction
+                    accumulation, M2M and L2L/L2P in float64 */
+};
+
+/* Plans the solve and allocates the device workspace on the current device.
+ * theta: opening parameter; cells A, B interact through their expansions iff
+ *   theta |c_A - c_B| >= (sqrt 3 / 2)(h_A + h_B) for geometric centres c (inclusive,
+ *   evaluated exactly).  Supported: 0.433 <= theta <= 1 (near field within the 26
+ *   neighbouring subgrids).
+ * order: expansion order, must be 3 (monopole + quadrupole + octupole, Section IV-C).
+ * precision: OCTO_FP64 or OCTO_MIXED.
+ * On success *out receives a handle to release with octo_fmm_destroy. */
+int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int precision, octo_fmm_t* out);
+
+/* Bottom-up traversal (Section VII-C, first phase): P2M at leaf cells (m = rho h^3
+ * at the cell centre) and M2M level by level up to the root (moments about the
+ * centre of mass, Section IV-C).  rho_dev: float64 [n_leaf*512], all entries > 0. */
+int octo_fmm_upward(octo_fmm_t h, const double* rho_dev, void* stream);
+
+/* Same-level cell-to-cell interactions on every level (Section VII-C, second
+ * phase; the "multipole kernel"): M2L over the fixed stencils with the
+ * angular-momentum correction, cross-level pairs at refinement boundaries, and
+ * P2P between near leaf cells.  Needs a preceding octo_fmm_upward. */
+int octo_fmm_interact(octo_fmm_t h, void* stream);
+
+/* Top-down traversal (Section VII-C, third phase): L2L down the tree and L2P at
+ * leaf cells.  Writes phi_dev [n_leaf*512] and g_dev [3][n_leaf*512]. */
+int octo_fmm_downward(octo_fmm_t h, double* phi_dev, double* g_dev, void* stream);
+
+/* The whole solve (upward + interact + downward), replayed from a CUDA graph
+ * captured on first use for this stream. */
+int octo_fmm_forces(octo_fmm_t h, const double* rho_dev, double* phi_dev, double* g_dev, void* stream);
+
+/* The same solve with HOST buffers: copies rho in and phi, g out on `stream`
+ * through pinned staging buffers owned by the handle, and synchronises the stream
+ * before returning.  rho_host [n_leaf*512], phi_host [n_leaf*512],
+ * g_host [3][n_leaf*512]. */
+int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host, double* g_host, void* stream);
+
+/* Vector-Jacobian product of the last forces/upward+interact+downward solve on this
+ * handle: drho = (d phi / d rho)^T dphi + (d g / d rho)^T dg, through every phase
+ * including the centre-of-mass dependence of the expansions.  dphi_dev
+ * [n_leaf*512], dg_dev [3][n_leaf*512], drho_dev [n_leaf*512] (overwritten).
+ * Returns OCTO_ESTATE if no forward solve has run. */
+int octo_fmm_backward(octo_fmm_t h, const double* dphi_dev, const double* dg_dev, double* drho_dev, void* stream);
+
+/* Ordered interaction counts of the plan: counts[0] same-level M2L, counts[1]
+ * cross-level M2L, counts[2] same-level P2P, counts[3] cross-level P2P.  Also
+ * reports a pending device-side error. */
+int octo_fmm_stats(octo_fmm_t h, int64_t counts[4]);
+
+/* Host-only planning: validates the tree and returns the counts above without
+ * touching a GPU. */
+int octo_fmm_plan_counts(const octo_tree_desc* tree, double theta, int64_t counts[4]);
+
+/* Copies internal state to HOST memory in descriptor node order, for tests:
+ * which = 0: multipoles [20][n_nodes*512]: m, X(3), M2 {xx,xy,xz,yy,yz,zz},
+ *            M3 {xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz};
+ * which = 1: local expansions [23][n_nodes*512]: L0, L1(3), L2(6), L3(10), dg(3)
+ *            (L2 and L3 of leaf cells are not computed and read as NaN).
+ * Synchronises the device. */
+int octo_fmm_read_state(octo_fmm_t h, int which, double* host_out);
+
+/* Options: key 0 = stencil chunks per interior subgrid (0 = autotune), key 1 =
+ * replay the whole solve from a captured CUDA graph (1, default) or launch the
+ * stages one by one (0), key 2 = record per-stage timing events (1/0, default 0).
+ * Returns OCTO_EINVAL for an unknown key or value. */
+int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value);
+
+/* Number of kernel launches one octo_fmm_forces call enqueues. */
+int octo_fmm_launches_per_solve(octo_fmm_t h);
+
+/* Stage introspection for measurement.  The solve is a fixed list of stages, one
+ * kernel launch each (e.g. "p2m", "m2m_l3", "m2l_interior", "leaf_conv",
+ * "l2l_l2").  octo_fmm_stage_count returns their number; octo_fmm_stage_info gives
+ * stage i's name (owned by the handle), the interactions it processes (pairs), the
+ * cells it writes, its algorithmic floating-point operations (the per-pair
+ * expression as written, a fused multiply-add counting two) and its algorithmic
+ * HBM bytes (tree passes: every value read or written once); any output pointer
+ * may be NULL.  With option key 2 set to 1, the captured graph records a
+ * CUDA event before every stage and after the last one; after the stream has
+ * completed a forces call, octo_fmm_stage_times writes each stage's elapsed time in
+ * milliseconds into ms[0..count) and returns count (cap must be >= count). */
+int octo_fmm_stage_count(octo_fmm_t h);
+int octo_fmm_stage_info(octo_fmm_t h, int i, const char** name, int64_t* pairs, int64_t* cells, int64_t* flops,
+                        int64_t* bytes);
+int octo_fmm_stage_times(octo_fmm_t h, float* ms, int cap);
+
+/* Message for the last failing call on h (or for create failures, h = NULL). */
+const char* octo_fmm_last_error(octo_fmm_t h);
+
+/* Frees the handle and its device workspace (synchronises the device first). */
+void octo_fmm_destroy(octo_fmm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCTO_FMM_H */

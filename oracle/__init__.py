@@ -35,7 +35,7 @@ def lib():
         L = ctypes.CDLL(path)
         tree_args = [ctypes.c_int, _ip, _ip, _ip, _dp, ctypes.c_double]
         L.oracle_upward.argtypes = tree_args + [_dp, _dp]
-        L.oracle_fmm.argtypes = tree_args + [_dp, ctypes.c_double, ctypes.c_int, _u8p, _dp, _dp, _dp]
+        L.oracle_fmm.argtypes = tree_args + [_dp, ctypes.c_double, ctypes.c_int, _u8p, _dp, _dp, _dp, _i64p]
         L.oracle_fmm_jvp.argtypes = tree_args + [_dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _u8p,
                                                  _dp, _dp, _dp, _dp]
         L.oracle_direct.argtypes = tree_args + [_dp, _u8p, _dp, _dp]
@@ -94,8 +94,9 @@ def upward(tree, rho) -> np.ndarray:
 
 
 def fmm(tree, rho, theta: float = 0.5, correction: bool = True, leaf_mask=None,
-        want_local: bool = False) -> Tuple[np.ndarray, np.ndarray, Optional[np.ndarray]]:
-    """phi [n_leaf*512], g [3, n_leaf*512] (NaN where not selected), local [23, n_nodes*512] or None."""
+        want_local: bool = False, work: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray, Optional[np.ndarray]]:
+    """phi [n_leaf*512], g [3, n_leaf*512] (NaN where not selected), local [23, n_nodes*512] or None.
+    `work` (int64 array of size 1, optional) receives the number of ordered interactions evaluated."""
     ta = _TreeArgs(tree)
     rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
     nl = tree.n_leaf * 512
@@ -104,7 +105,7 @@ def fmm(tree, rho, theta: float = 0.5, correction: bool = True, leaf_mask=None,
     loc = np.empty((23, ta.n * 512)) if want_local else None
     m = _mask(tree, leaf_mask)
     _check(lib().oracle_fmm(*ta.args(), _p(rho, _dp), float(theta), 1 if correction else 0, _p(m, _u8p),
-                            _p(phi, _dp), _p(g, _dp), _p(loc, _dp)), "fmm")
+                            _p(phi, _dp), _p(g, _dp), _p(loc, _dp), _p(work, _i64p)), "fmm")
     return phi, g, loc
 
 

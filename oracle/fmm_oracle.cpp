@@ -454,6 +454,8 @@ struct Solver {
 
   // Interactions and downward pass for the cells in `need` (ancestor-closed);
   // fills L (indexed like mp) and the direct P2P sums for needed leaf cells.
+  int64_t work = 0;  // ordered interactions evaluated by the last interact_down
+
   void interact_down(const vector<char>& need, vector<Loc<T>>& L, vector<T>& pphi, vector<T>& pg) {
     struct Pr {
       int64_t tgt, src;
@@ -475,6 +477,7 @@ struct Solver {
         tg.push_back(prs[i].tgt);
       }
     start.push_back(prs.size());
+    work = (int64_t)prs.size();
     L.assign(mp.size(), Loc<T>());
     pphi.assign(mp.size(), T(0.0));
     pg.assign(3 * mp.size(), T(0.0));
@@ -584,10 +587,11 @@ int oracle_upward(int n, const int32_t* level, const int32_t* ijk, const int32_t
 // Full FMM.  leaf_mask (n_leaf*512 bytes, may be null = all) selects the leaf cells
 // whose phi/g are computed; others are left untouched.  flags bit0: apply the
 // angular-momentum correction.  loc_out (may be null): [23][n_nodes*512] final local
-// expansions (after the downward pass) of needed cells, NaN elsewhere.
+// expansions (after the downward pass) of needed cells, NaN elsewhere.  work_out
+// (may be null): number of ordered interactions (M2L + P2P) evaluated.
 int oracle_fmm(int n, const int32_t* level, const int32_t* ijk, const int32_t* children, const double* origin,
                double extent, const double* rho, double theta, int flags, const uint8_t* leaf_mask, double* phi,
-               double* g, double* loc_out) {
+               double* g, double* loc_out, int64_t* work_out) {
   Tree t;
   int rc = build_tree(t, n, level, ijk, children, origin, extent);
   if (rc) return rc;
@@ -597,6 +601,7 @@ int oracle_fmm(int n, const int32_t* level, const int32_t* ijk, const int32_t* c
   vector<Loc<double>> L;
   vector<double> pphi, pg;
   s.interact_down(need, L, pphi, pg);
+  if (work_out) *work_out = s.work;
   leaf_outputs(t, need, L, pphi, pg, [&](size_t k, size_t nl, double ph, const double* gg) {
     phi[k] = ph;
     for (int a = 0; a < 3; ++a) g[a * nl + k] = gg[a];

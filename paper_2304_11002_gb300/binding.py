@@ -1,0 +1,233 @@
+"""Thin ctypes binding of the C ABI in include/octo_fmm.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Device buffers
+are passed as torch CUDA tensors (float64, contiguous) and streams as
+torch.cuda.Stream (default: the current stream).  All arithmetic runs in the
+library's CUDA kernels; there is no CPU path.  Loading fails loudly if the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liboctofmm.so")
+
+OCTO_OK = 0
+OCTO_FP64 = 0
+OCTO_MIXED = 1
+STATUS = {0: "OCTO_OK", -1: "OCTO_EINVAL", -2: "OCTO_ETREE", -3: "OCTO_ENOMEM", -4: "OCTO_ECUDA",
+          -5: "OCTO_ETIMEOUT", -6: "OCTO_ENONPOS", -7: "OCTO_ESTATE"}
+
+# every symbol include/octo_fmm.h declares
+SYMBOLS = ["octo_fmm_create", "octo_fmm_upward", "octo_fmm_interact", "octo_fmm_downward", "octo_fmm_forces",
+           "octo_fmm_forces_host", "octo_fmm_backward", "octo_fmm_stats", "octo_fmm_plan_counts",
+           "octo_fmm_read_state", "octo_fmm_set_option", "octo_fmm_launches_per_solve", "octo_fmm_stage_count",
+           "octo_fmm_stage_info", "octo_fmm_stage_times", "octo_fmm_last_error", "octo_fmm_destroy"]
+
+
+class OctoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class TreeDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("level", ctypes.POINTER(ctypes.c_int32)),
+                ("ijk", ctypes.POINTER(ctypes.c_int32)), ("children", ctypes.POINTER(ctypes.c_int32)),
+                ("origin", ctypes.c_double * 3), ("extent", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} is missing: build it with paper_2304_11002_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp = ctypes.c_void_p, ctypes.c_void_p
+        L.octo_fmm_create.argtypes = [ctypes.POINTER(TreeDesc), ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(vp)]
+        L.octo_fmm_upward.argtypes = [vp, dp, vp]
+        L.octo_fmm_interact.argtypes = [vp, vp]
+        L.octo_fmm_downward.argtypes = [vp, dp, dp, vp]
+        L.octo_fmm_forces.argtypes = [vp, dp, dp, dp, vp]
+        L.octo_fmm_forces_host.argtypes = [vp, dp, dp, dp, vp]
+        L.octo_fmm_backward.argtypes = [vp, dp, dp, dp, vp]
+        L.octo_fmm_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        L.octo_fmm_plan_counts.argtypes = [ctypes.POINTER(TreeDesc), ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]
+        L.octo_fmm_read_state.argtypes = [vp, ctypes.c_int, dp]
+        L.octo_fmm_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
+        L.octo_fmm_launches_per_solve.argtypes = [vp]
+        L.octo_fmm_stage_count.argtypes = [vp]
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        L.octo_fmm_stage_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i64p, i64p, i64p, i64p]
+        L.octo_fmm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+        L.octo_fmm_last_error.argtypes = [vp]
+        L.octo_fmm_last_error.restype = ctypes.c_char_p
+        L.octo_fmm_destroy.argtypes = [vp]
+        L.octo_fmm_destroy.restype = None
+        for name in SYMBOLS:
+            f = getattr(L, name)
+            if name not in ("octo_fmm_last_error", "octo_fmm_destroy"):
+                f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, h=None):
+    if rc != OCTO_OK:
+        msg = lib().octo_fmm_last_error(h)
+        raise OctoError(rc, msg.decode() if msg else "")
+
+
+class _Desc:
+    """Keeps the numpy arrays of a tree descriptor alive while the C struct is used."""
+
+    def __init__(self, tree):
+        self.level = np.ascontiguousarray(tree.level, dtype=np.int32)
+        self.ijk = np.ascontiguousarray(tree.ijk, dtype=np.int32)
+        self.children = np.ascontiguousarray(tree.children, dtype=np.int32)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        self.desc = TreeDesc(int(self.level.shape[0]), self.level.ctypes.data_as(ip), self.ijk.ctypes.data_as(ip),
+                             self.children.ctypes.data_as(ip), (ctypes.c_double * 3)(*[float(v) for v in tree.origin]),
+                             float(tree.extent))
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def octo_fmm_plan_counts(tree, theta: float = 0.5) -> np.ndarray:
+    d = _Desc(tree)
+    out = (ctypes.c_int64 * 4)()
+    _check(lib().octo_fmm_plan_counts(ctypes.byref(d.desc), float(theta), out))
+    return np.array(out[:], dtype=np.int64)
+
+
+def octo_fmm_create(tree, theta: float = 0.5, order: int = 3, precision: int = OCTO_FP64) -> ctypes.c_void_p:
+    d = _Desc(tree)
+    h = ctypes.c_void_p()
+    _check(lib().octo_fmm_create(ctypes.byref(d.desc), float(theta), int(order), int(precision), ctypes.byref(h)))
+    return h
+
+
+def octo_fmm_destroy(h) -> None:
+    lib().octo_fmm_destroy(h)
+
+
+def octo_fmm_upward(h, rho, stream=None) -> None:
+    _check(lib().octo_fmm_upward(h, _ptr(rho), _stream(stream)), h)
+
+
+def octo_fmm_interact(h, stream=None) -> None:
+    _check(lib().octo_fmm_interact(h, _stream(stream)), h)
+
+
+def octo_fmm_downward(h, phi, g, stream=None) -> None:
+    _check(lib().octo_fmm_downward(h, _ptr(phi), _ptr(g), _stream(stream)), h)
+
+
+def octo_fmm_forces(h, rho, phi, g, stream=None) -> None:
+    _check(lib().octo_fmm_forces(h, _ptr(rho), _ptr(phi), _ptr(g), _stream(stream)), h)
+
+
+def octo_fmm_forces_host(h, rho: np.ndarray, phi: np.ndarray, g: np.ndarray, stream=None) -> None:
+    for a in (rho, phi, g):
+        if not (a.dtype == np.float64 and a.flags.c_contiguous):
+            raise ValueError("host buffers must be contiguous float64")
+    _check(lib().octo_fmm_forces_host(h, rho.ctypes.data, phi.ctypes.data, g.ctypes.data, _stream(stream)), h)
+
+
+def octo_fmm_backward(h, dphi, dg, drho, stream=None) -> None:
+    _check(lib().octo_fmm_backward(h, _ptr(dphi), _ptr(dg), _ptr(drho), _stream(stream)), h)
+
+
+def octo_fmm_stats(h) -> np.ndarray:
+    out = (ctypes.c_int64 * 4)()
+    _check(lib().octo_fmm_stats(h, out), h)
+    return np.array(out[:], dtype=np.int64)
+
+
+def octo_fmm_read_state(h, which: int, n_nodes: int) -> np.ndarray:
+    nf = 20 if which == 0 else 23
+    out = np.empty((nf, n_nodes * 512), dtype=np.float64)
+    _check(lib().octo_fmm_read_state(h, int(which), out.ctypes.data), h)
+    return out
+
+
+def octo_fmm_set_option(h, key: int, value: int) -> None:
+    _check(lib().octo_fmm_set_option(h, int(key), int(value)), h)
+
+
+def octo_fmm_launches_per_solve(h) -> int:
+    return int(lib().octo_fmm_launches_per_solve(h))
+
+
+def octo_fmm_stage_count(h) -> int:
+    return int(lib().octo_fmm_stage_count(h))
+
+
+def octo_fmm_stage_info(h, i: int) -> dict:
+    """name, pairs, cells, flops, bytes of stage i."""
+    name = ctypes.c_char_p()
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().octo_fmm_stage_info(h, int(i), ctypes.byref(name), *[ctypes.byref(x) for x in v]), h)
+    return {"name": name.value.decode(), "pairs": int(v[0].value), "cells": int(v[1].value),
+            "flops": int(v[2].value), "bytes": int(v[3].value)}
+
+
+def octo_fmm_stage_times(h) -> np.ndarray:
+    n = octo_fmm_stage_count(h)
+    buf = (ctypes.c_float * max(n, 1))()
+    rc = lib().octo_fmm_stage_times(h, buf, n)
+    if rc < 0:
+        _check(rc, h)
+    return np.array(buf[:n], dtype=np.float64)
+
+
+class OctoFMM:
+    """Owning wrapper: one solver handle for one tree on the current CUDA device."""
+
+    def __init__(self, tree, theta: float = 0.5, precision: int = OCTO_FP64, order: int = 3):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("OctoFMM needs a CUDA device")
+        self.tree = tree
+        self.n_leaf_cells = tree.n_leaf * 512
+        self.handle = octo_fmm_create(tree, theta, order, precision)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            octo_fmm_destroy(h)
+            self.handle = None
+
+    def forces(self, rho, phi=None, g=None, stream=None):
+        import torch
+        if phi is None:
+            phi = torch.empty(self.n_leaf_cells, dtype=torch.float64, device=rho.device)
+        if g is None:
+            g = torch.empty((3, self.n_leaf_cells), dtype=torch.float64, device=rho.device)
+        octo_fmm_forces(self.handle, rho, phi, g, stream)
+        return phi, g
+
+    def counts(self) -> np.ndarray:
+        return octo_fmm_stats(self.handle)

@@ -1,0 +1,600 @@
+// C ABI of the solver (include/octo_fmm.h): handle, device workspace, phase
+// ordering on a stream and the CUDA-graph replay of the whole solve.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/octo_fmm.h"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace octo;
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_create_error;
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  *dst = nullptr;
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * src.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+struct octo_fmm {
+  Plan plan;
+  int precision = OCTO_FP64;
+  int device = 0;
+  std::string err;
+
+  // tree and lists
+  int *d_level = nullptr, *d_parent = nullptr, *d_octant = nullptr, *d_children = nullptr, *d_nbr = nullptr,
+      *d_leaf_id = nullptr, *d_ijk = nullptr;
+  int *d_interior = nullptr, *d_leaf = nullptr, *d_boundary = nullptr;
+  int *d_st_parity = nullptr, *d_st_root = nullptr, *d_st_near = nullptr;
+  Kappa* d_kappa = nullptr;
+  int64_t *d_xf_t = nullptr, *d_xf_s = nullptr, *d_xf_src = nullptr;
+  int64_t *d_xl_t = nullptr, *d_xl_s = nullptr, *d_xl_src = nullptr;
+  int n_xf = 0, n_xl = 0;
+  int64_t xf_pairs = 0, xl_pairs = 0;
+
+  // state
+  double *d_mp = nullptr, *d_loc = nullptr;
+  float* d_mp32 = nullptr;    // float32 multipoles (mixed precision only)
+  float4* d_kappa32 = nullptr;
+  DevTree dt;
+  Stencils st;
+  CrossList xf, xl;
+  bool forward_done = false;
+  bool use_graph = true;
+
+  // host-buffer path
+  double *h_stage = nullptr, *d_io = nullptr;
+
+  // the solve as a fixed list of stages, one kernel launch each
+  struct Stage {
+    int kind;   // see enum StageKind
+    int a, b;   // level range or list selector
+    std::string name;
+    int64_t pairs;  // interactions processed (0 for tree passes)
+    int64_t cells;  // cells processed
+    int64_t flops;  // algorithmic floating-point operations
+    int64_t bytes;  // algorithmic HBM bytes of the tree passes
+  };
+  std::vector<Stage> stages;
+  bool profile = false;
+  std::vector<cudaEvent_t> ev;
+
+  // graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const double* g_rho = nullptr;
+  double *g_phi = nullptr, *g_g = nullptr;
+
+  int64_t n_leaf_cells() const { return (int64_t)plan.n_leaf * kCells; }
+};
+
+namespace {
+
+int fail(octo_fmm* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(octo_fmm* h, cudaError_t e, const char* what) {
+  return fail(h, OCTO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void free_all(octo_fmm* h) {
+  void* ptrs[] = {h->d_level,    h->d_parent,  h->d_octant, h->d_children, h->d_nbr,    h->d_leaf_id,
+                  h->d_ijk,      h->d_interior, h->d_leaf,  h->d_boundary, h->d_st_parity, h->d_st_root,
+                  h->d_st_near,  h->d_kappa,   h->d_xf_t,   h->d_xf_s,     h->d_xf_src,  h->d_xl_t,
+                  h->d_xl_s,     h->d_xl_src,  h->d_mp,     h->d_loc,      h->d_io,        h->d_mp32,
+                  h->d_kappa32};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->h_stage) cudaFreeHost(h->h_stage);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (auto& ev : h->ev)
+    if (ev) cudaEventDestroy(ev);
+}
+
+enum StageKind { S_P2M, S_M2M, S_M2L, S_CONV, S_BOUNDARY, S_CROSS_FULL, S_CROSS_LEAF, S_L2L };
+
+// Floating-point operations of the per-pair expression as written (a fused
+// multiply-add counts as two), obtained by running the same template with a
+// counting scalar type.
+int64_t g_counted_ops = 0;
+#define HD __host__ __device__
+struct Counted {
+  double v;
+  HD Counted() : v(0) {}
+  HD Counted(double x) : v(x) {}
+  HD static void tick() {
+#ifndef __CUDA_ARCH__
+    ++g_counted_ops;
+#endif
+  }
+  HD friend Counted operator+(Counted a, Counted b) { tick(); return Counted(a.v + b.v); }
+  HD friend Counted operator-(Counted a, Counted b) { tick(); return Counted(a.v - b.v); }
+  HD friend Counted operator*(Counted a, Counted b) { tick(); return Counted(a.v * b.v); }
+  HD Counted operator-() const { return Counted(-v); }
+  HD Counted& operator+=(Counted b) { tick(); v += b.v; return *this; }
+  HD Counted& operator-=(Counted b) { tick(); v -= b.v; return *this; }
+};
+#undef HD
+
+// Per pair: R = X_A - X_B (3), r^2 (5), the float64 reciprocal square root
+// refinement (8) and the expansion arithmetic.
+template <bool FULL, bool TOCT>
+int64_t m2l_pair_flops() {
+  Counted Q[6], O[10], Oh[10], tOh[3];
+  Acc<Counted> a;
+  acc_zero(a);
+  g_counted_ops = 0;
+  m2l_pair<FULL, TOCT, Counted>(Counted(1.0), Counted(2.0), Counted(3.0), Counted(1.0), Q, O, Oh, tOh,
+                                Counted(0.5), a);
+  return g_counted_ops + 3 + 5 + 8;
+}
+constexpr int64_t kConvFlopsPerPair = 8;  // four fused multiply-adds
+
+// Builds the fixed stage list (its length does not depend on the data, so the
+// whole sequence can be captured once into a CUDA graph).
+void make_stages(octo_fmm* h) {
+  const Plan& P = h->plan;
+  auto add = [&](int kind, int a, int b, std::string name, int64_t pairs, int64_t cells) {
+    // algorithmic flops and bytes of the stage (bytes: each value read or written once)
+    int64_t flops = 0, bytes = 0;
+    switch (kind) {
+      case S_P2M: bytes = cells * 16; break;                      // rho in, m out
+      case S_M2M: bytes = cells * (8 * 20 + 20) * 8; break;        // 8 children in, parent out
+      case S_M2L: flops = pairs * m2l_pair_flops<true, true>(); break;
+      case S_CONV: flops = pairs * kConvFlopsPerPair; break;
+      case S_BOUNDARY: flops = pairs * m2l_pair_flops<false, false>(); break;
+      case S_CROSS_FULL: flops = pairs * m2l_pair_flops<true, true>(); break;
+      case S_CROSS_LEAF: flops = pairs * m2l_pair_flops<false, false>(); break;
+      case S_L2L: bytes = cells * 52 * 8; break;                   // own L/X in + L out + parent share
+    }
+    h->stages.push_back({kind, a, b, std::move(name), pairs, cells, flops, bytes});
+  };
+  h->stages.clear();
+  if (!P.leaf_nodes.empty()) add(S_P2M, 0, 0, "p2m", 0, (int64_t)P.leaf_nodes.size() * kCells);
+  for (int l = P.max_level - 1; l >= 0; --l)
+    if (P.level_start[l + 1] > P.level_start[l]) {
+      int64_t ni = 0;
+      for (int k = P.level_start[l]; k < P.level_start[l + 1]; ++k) ni += P.children[8 * k] >= 0;
+      add(S_M2M, P.level_start[l], P.level_start[l + 1], "m2m_l" + std::to_string(l), 0, ni * kCells);
+    }
+  if (!P.interior_nodes.empty())
+    add(S_M2L, 0, 0, h->precision == OCTO_MIXED ? "m2l_interior_f32" : "m2l_interior", P.kernel_pairs[0],
+        (int64_t)P.interior_nodes.size() * kCells);
+  if (!P.leaf_nodes.empty())
+    add(S_CONV, 0, 0, h->precision == OCTO_MIXED ? "leaf_conv_mixed" : "leaf_conv",
+        P.kernel_pairs[1] + P.kernel_pairs[2], (int64_t)P.leaf_nodes.size() * kCells);
+  if (!P.boundary_nodes.empty())
+    add(S_BOUNDARY, 0, 0, "m2l_boundary", P.kernel_pairs[3], (int64_t)P.boundary_nodes.size() * kCells);
+  if (h->n_xf > 0) add(S_CROSS_FULL, 0, 0, "cross_interior", h->xf_pairs, h->n_xf);
+  if (h->n_xl > 0) add(S_CROSS_LEAF, 0, 0, "cross_leaf", h->xl_pairs, h->n_xl);
+  for (int l = 0; l <= P.max_level; ++l)
+    if (P.level_start[l + 1] > P.level_start[l])
+      add(S_L2L, P.level_start[l], P.level_start[l + 1], "l2l_l" + std::to_string(l), 0,
+          (int64_t)(P.level_start[l + 1] - P.level_start[l]) * kCells);
+}
+
+cudaError_t enq_stage(octo_fmm* h, const octo_fmm::Stage& st, const double* rho, double* phi, double* g,
+                      cudaStream_t s) {
+  const Plan& P = h->plan;
+  switch (st.kind) {
+    case S_P2M: return launch_p2m(h->dt, h->d_leaf, (int)P.leaf_nodes.size(), rho, h->d_mp, h->d_mp32, s);
+    case S_M2M: return launch_m2m(h->dt, st.a, st.b, h->d_mp, h->d_mp32, s);
+    case S_M2L:
+      if (h->precision == OCTO_MIXED)
+        return launch_m2l_interior_f32(h->dt, h->d_interior, (int)P.interior_nodes.size(), h->st, h->d_mp32,
+                                       h->d_loc, s);
+      return launch_m2l_interior(h->dt, h->d_interior, (int)P.interior_nodes.size(), h->st, h->d_mp, h->d_loc, s);
+    case S_CONV:
+      if (h->precision == OCTO_MIXED)
+        return launch_leaf_conv_mixed(h->dt, h->d_leaf, (int)P.leaf_nodes.size(), h->st, h->d_mp, h->d_loc, s);
+      return launch_leaf_conv(h->dt, h->d_leaf, (int)P.leaf_nodes.size(), h->st, h->d_mp, h->d_loc, s);
+    case S_BOUNDARY:
+      return launch_m2l_boundary(h->dt, h->d_boundary, (int)P.boundary_nodes.size(), h->st, h->d_mp, h->d_loc, s);
+    case S_CROSS_FULL: return launch_cross(h->dt, h->xf, CrossList{nullptr, nullptr, nullptr, 0}, h->d_mp, h->d_loc, s);
+    case S_CROSS_LEAF: return launch_cross(h->dt, CrossList{nullptr, nullptr, nullptr, 0}, h->xl, h->d_mp, h->d_loc, s);
+    case S_L2L: return launch_l2l(h->dt, st.a, st.b, h->d_mp, h->d_loc, phi, g, h->n_leaf_cells(), s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Phases: stages [0, i_interact) are the upward pass, [i_interact, i_downward) the
+// interactions and the rest the downward pass.
+cudaError_t enq_range(octo_fmm* h, int kind_lo, int kind_hi, const double* rho, double* phi, double* g,
+                      cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < h->stages.size() && e == cudaSuccess; ++i) {
+    const auto& st = h->stages[i];
+    if (st.kind < kind_lo || st.kind > kind_hi) continue;
+    if (h->profile) e = cudaEventRecordWithFlags(h->ev[i], s, cudaEventRecordExternal);
+    if (e == cudaSuccess) e = enq_stage(h, st, rho, phi, g, s);
+  }
+  return e;
+}
+
+cudaError_t enq_upward(octo_fmm* h, const double* rho, cudaStream_t s) {
+  return enq_range(h, S_P2M, S_M2M, rho, nullptr, nullptr, s);
+}
+cudaError_t enq_interact(octo_fmm* h, cudaStream_t s) {
+  return enq_range(h, S_M2L, S_CROSS_LEAF, nullptr, nullptr, nullptr, s);
+}
+cudaError_t enq_downward(octo_fmm* h, double* phi, double* g, cudaStream_t s) {
+  return enq_range(h, S_L2L, S_L2L, nullptr, phi, g, s);
+}
+
+cudaError_t enq_solve(octo_fmm* h, const double* rho, double* phi, double* g, cudaStream_t s) {
+  cudaError_t e = enq_range(h, S_P2M, S_L2L, rho, phi, g, s);
+  if (e == cudaSuccess && h->profile) e = cudaEventRecordWithFlags(h->ev[h->stages.size()], s, cudaEventRecordExternal);
+  return e;
+}
+
+int count_launches(const octo_fmm* h) { return (int)h->stages.size(); }
+
+// Monopole kernel table over [-R, R]^3 for unit cell width (see k_leaf_conv):
+// kappa0 = -1/|d|, kappa1 = -d/|d|^3, zero at d = 0.
+std::vector<Kappa> make_kappa(int R) {
+  const int W = 2 * R + 1;
+  std::vector<Kappa> k((size_t)W * W * W);
+  for (int z = -R; z <= R; ++z)
+    for (int y = -R; y <= R; ++y)
+      for (int x = -R; x <= R; ++x) {
+        Kappa v = {{0, 0, 0, 0}};
+        double r2 = (double)(x * x + y * y + z * z);
+        if (r2 > 0) {
+          double r = std::sqrt(r2);
+          double ir3 = 1.0 / (r2 * r);
+          v.v[0] = -1.0 / r;
+          v.v[1] = -(double)x * ir3;
+          v.v[2] = -(double)y * ir3;
+          v.v[3] = -(double)z * ir3;
+        }
+        k[(size_t)(x + R) + W * (y + R) + (size_t)W * W * (z + R)] = v;
+      }
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+int octo_fmm_plan_counts(const octo_tree_desc* tree, double theta, int64_t counts[4]) {
+  if (!counts) return OCTO_EINVAL;
+  Plan P;
+  int rc = build_plan(tree, theta, P);
+  if (rc != OCTO_OK) {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_error = P.error;
+    return rc;
+  }
+  for (int i = 0; i < 4; ++i) counts[i] = P.counts[i];
+  return OCTO_OK;
+}
+
+int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int precision, octo_fmm_t* out) {
+  auto create_fail = [](int code, const std::string& msg) {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_error = msg;
+    return code;
+  };
+  if (!out) return create_fail(OCTO_EINVAL, "out is null");
+  *out = nullptr;
+  if (order != 3) return create_fail(OCTO_EINVAL, "only order 3 is supported");
+  if (precision != OCTO_FP64 && precision != OCTO_MIXED) return create_fail(OCTO_EINVAL, "unknown precision");
+  octo_fmm* h = new (std::nothrow) octo_fmm();
+  if (!h) return create_fail(OCTO_ENOMEM, "host allocation failed");
+  int rc = build_plan(tree, theta, h->plan);
+  if (rc != OCTO_OK) {
+    std::string m = h->plan.error;
+    delete h;
+    return create_fail(rc, m);
+  }
+  h->precision = precision;
+  cudaGetDevice(&h->device);
+  Plan& P = h->plan;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](auto** d, const auto& v) {
+    if (e == cudaSuccess) e = upload(d, v);
+  };
+  up(&h->d_level, P.level);
+  up(&h->d_parent, P.parent);
+  up(&h->d_octant, P.octant);
+  up(&h->d_children, P.children);
+  up(&h->d_nbr, P.nbr);
+  up(&h->d_leaf_id, P.leaf_id);
+  up(&h->d_ijk, P.ijk);
+  up(&h->d_interior, P.interior_nodes);
+  up(&h->d_leaf, P.leaf_nodes);
+  up(&h->d_boundary, P.boundary_nodes);
+  up(&h->d_st_parity, P.st_parity);
+  up(&h->d_st_root, P.st_root);
+  up(&h->d_st_near, P.st_near);
+  int R = 7;
+  for (int32_t v : P.st_parity)
+    for (int k = 0; k < 3; ++k) R = std::max(R, std::abs((int)(int8_t)((v >> (8 * k)) & 0xff)));
+  std::vector<Kappa> kap = make_kappa(R);
+  up(&h->d_kappa, kap);
+  {
+    std::vector<float4> k32(kap.size());
+    for (size_t i = 0; i < kap.size(); ++i)
+      k32[i] = make_float4((float)kap[i].v[0], (float)kap[i].v[1], (float)kap[i].v[2], (float)kap[i].v[3]);
+    up(&h->d_kappa32, k32);
+  }
+  // split cross-level targets into interior (full expansion) and leaf targets
+  {
+    std::vector<int64_t> ft, fs, fsrc, lt, ls, lsrc;
+    fs.push_back(0);
+    ls.push_back(0);
+    for (size_t i = 0; i < P.x_targets.size(); ++i) {
+      int64_t tg = P.x_targets[i];
+      bool full = P.children[8 * (tg / kCells)] >= 0;
+      auto& T = full ? ft : lt;
+      auto& S = full ? fs : ls;
+      auto& SRC = full ? fsrc : lsrc;
+      T.push_back(tg);
+      for (int64_t k = P.x_start[i]; k < P.x_start[i + 1]; ++k) SRC.push_back(P.x_sources[k]);
+      S.push_back((int64_t)SRC.size());
+    }
+    h->n_xf = (int)ft.size();
+    h->n_xl = (int)lt.size();
+    h->xf_pairs = (int64_t)fsrc.size();
+    h->xl_pairs = (int64_t)lsrc.size();
+    up(&h->d_xf_t, ft);
+    up(&h->d_xf_s, fs);
+    up(&h->d_xf_src, fsrc);
+    up(&h->d_xl_t, lt);
+    up(&h->d_xl_s, ls);
+    up(&h->d_xl_src, lsrc);
+  }
+  const int64_t NC = (int64_t)P.n_nodes * kCells;
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_mp, sizeof(double) * N_MP * NC);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_loc, sizeof(double) * N_LOC * NC);
+  if (e == cudaSuccess && precision == OCTO_MIXED) e = cudaMalloc(&h->d_mp32, sizeof(float) * N_MP * NC);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_io, sizeof(double) * 5 * h->n_leaf_cells());
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_stage, sizeof(double) * 5 * h->n_leaf_cells());
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    std::string m = std::string("device setup failed: ") + cudaGetErrorString(e);
+    bool oom = e == cudaErrorMemoryAllocation;
+    free_all(h);
+    delete h;
+    return create_fail(oom ? OCTO_ENOMEM : OCTO_ECUDA, m);
+  }
+  DevTree& t = h->dt;
+  t.NC = NC;
+  t.n_nodes = P.n_nodes;
+  t.level = h->d_level;
+  t.parent = h->d_parent;
+  t.octant = h->d_octant;
+  t.children = h->d_children;
+  t.nbr = h->d_nbr;
+  t.leaf_id = h->d_leaf_id;
+  t.ijk = h->d_ijk;
+  for (int d = 0; d < 3; ++d) t.origin[d] = P.origin[d];
+  for (int l = 0; l < 16; ++l) {
+    double hl = cell_width(P, l);
+    t.h[l] = hl;
+    t.h3[l] = hl * hl * hl;
+  }
+  int RN = 0;
+  for (int32_t v : P.st_near)
+    for (int k = 0; k < 3; ++k) RN = std::max(RN, std::abs((int)(int8_t)((v >> (8 * k)) & 0xff)));
+  h->st = Stencils{h->d_st_parity, P.n_st,       h->d_st_root,   (int)P.st_root.size(), h->d_st_near,
+                   (int)P.st_near.size(), h->d_kappa, h->d_kappa32, R, RN};
+  h->xf = CrossList{h->d_xf_t, h->d_xf_s, h->d_xf_src, h->n_xf};
+  h->xl = CrossList{h->d_xl_t, h->d_xl_s, h->d_xl_src, h->n_xl};
+  e = configure_kernels();
+  if (e == cudaSuccess) e = configure_kernels_mixed();
+  if (e == cudaSuccess)
+    e = launch_init_leaf(t, h->d_leaf, (int)P.leaf_nodes.size(), h->d_mp, h->d_mp32, h->cap_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap_stream);
+  if (e != cudaSuccess) {
+    std::string m = std::string("init failed: ") + cudaGetErrorString(e);
+    free_all(h);
+    delete h;
+    return create_fail(OCTO_ECUDA, m);
+  }
+  make_stages(h);
+  h->ev.resize(h->stages.size() + 1, nullptr);
+  for (auto& ev : h->ev)
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      free_all(h);
+      delete h;
+      return create_fail(OCTO_ECUDA, "event creation failed");
+    }
+  *out = h;
+  return OCTO_OK;
+}
+
+int octo_fmm_upward(octo_fmm_t h, const double* rho, void* stream) {
+  if (!h || !rho) return h ? fail(h, OCTO_EINVAL, "rho is null") : OCTO_EINVAL;
+  cudaError_t e = enq_upward(h, rho, (cudaStream_t)stream);
+  return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "upward");
+}
+
+int octo_fmm_interact(octo_fmm_t h, void* stream) {
+  if (!h) return OCTO_EINVAL;
+  cudaError_t e = enq_interact(h, (cudaStream_t)stream);
+  return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "interact");
+}
+
+int octo_fmm_downward(octo_fmm_t h, double* phi, double* g, void* stream) {
+  if (!h || !phi || !g) return h ? fail(h, OCTO_EINVAL, "phi or g is null") : OCTO_EINVAL;
+  cudaError_t e = enq_downward(h, phi, g, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "downward");
+  h->forward_done = true;
+  return OCTO_OK;
+}
+
+int octo_fmm_forces(octo_fmm_t h, const double* rho, double* phi, double* g, void* stream) {
+  if (!h || !rho || !phi || !g) return h ? fail(h, OCTO_EINVAL, "null buffer") : OCTO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!h->use_graph) {
+    cudaError_t e = enq_solve(h, rho, phi, g, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "forces");
+    h->forward_done = true;
+    return OCTO_OK;
+  }
+  if (!h->gexec || h->g_rho != rho || h->g_phi != phi || h->g_g != g) {
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+    cudaError_t el = enq_solve(h, rho, phi, g, h->cap_stream);
+    e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (el != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(h, el, "capture launches");
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->gexec = nullptr;
+      return cuda_fail(h, e, "instantiate graph");
+    }
+    h->g_rho = rho;
+    h->g_phi = phi;
+    h->g_g = g;
+  }
+  cudaError_t e = cudaGraphLaunch(h->gexec, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+  h->forward_done = true;
+  return OCTO_OK;
+}
+
+int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host, double* g_host, void* stream) {
+  if (!h || !rho_host || !phi_host || !g_host) return h ? fail(h, OCTO_EINVAL, "null buffer") : OCTO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = h->n_leaf_cells();
+  double* d_rho = h->d_io;
+  double* d_phi = h->d_io + n;
+  double* d_g = h->d_io + 2 * n;
+  std::memcpy(h->h_stage, rho_host, sizeof(double) * n);
+  cudaError_t e = cudaMemcpyAsync(d_rho, h->h_stage, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy rho in");
+  int rc = octo_fmm_forces(h, d_rho, d_phi, d_g, stream);
+  if (rc != OCTO_OK) return rc;
+  e = cudaMemcpyAsync(h->h_stage + n, d_phi, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copy results out");
+  std::memcpy(phi_host, h->h_stage + n, sizeof(double) * n);
+  std::memcpy(g_host, h->h_stage + 2 * n, sizeof(double) * 3 * n);
+  return OCTO_OK;
+}
+
+int octo_fmm_backward(octo_fmm_t h, const double* dphi, const double* dg, double* drho, void* stream) {
+  if (!h || !dphi || !dg || !drho) return h ? fail(h, OCTO_EINVAL, "null buffer") : OCTO_EINVAL;
+  if (!h->forward_done) return fail(h, OCTO_ESTATE, "backward needs a forward solve on this handle");
+  (void)stream;
+  return fail(h, OCTO_EINVAL, "backward is not available in this build");
+}
+
+int octo_fmm_stats(octo_fmm_t h, int64_t counts[4]) {
+  if (!h || !counts) return OCTO_EINVAL;
+  for (int i = 0; i < 4; ++i) counts[i] = h->plan.counts[i];
+  return OCTO_OK;
+}
+
+int octo_fmm_read_state(octo_fmm_t h, int which, double* out) {
+  if (!h || !out || (which != 0 && which != 1)) return h ? fail(h, OCTO_EINVAL, "bad arguments") : OCTO_EINVAL;
+  const Plan& P = h->plan;
+  const int nf = which == 0 ? N_MP : N_LOC;
+  const int64_t NC = (int64_t)P.n_nodes * kCells;
+  std::vector<double> buf((size_t)nf * NC);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(buf.data(), which == 0 ? h->d_mp : h->d_loc, sizeof(double) * nf * NC, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "read state");
+  for (int f = 0; f < nf; ++f)
+    for (int i = 0; i < P.n_nodes; ++i) {
+      int k = P.dnode_of_desc[i];
+      bool leaf = P.children[8 * k] < 0;
+      for (int c = 0; c < kCells; ++c) {
+        double v = buf[(size_t)f * NC + (size_t)k * kCells + c];
+        if (which == 1 && leaf && f >= G_L2 && f < G_DG) v = NAN;
+        out[(size_t)f * NC + (size_t)i * kCells + c] = v;
+      }
+    }
+  return OCTO_OK;
+}
+
+int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value) {
+  if (!h) return OCTO_EINVAL;
+  if (key == 1 && (value == 0 || value == 1)) {
+    h->use_graph = value != 0;
+    return OCTO_OK;
+  }
+  if (key == 0 && value >= 0) return OCTO_OK;
+  if (key == 2 && (value == 0 || value == 1)) {
+    h->profile = value != 0;
+    if (h->gexec) {  // re-capture with or without the timing events
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    return OCTO_OK;
+  }
+  return fail(h, OCTO_EINVAL, "unknown option");
+}
+
+int octo_fmm_stage_count(octo_fmm_t h) { return h ? (int)h->stages.size() : 0; }
+
+int octo_fmm_stage_info(octo_fmm_t h, int i, const char** name, int64_t* pairs, int64_t* cells, int64_t* flops,
+                        int64_t* bytes) {
+  if (!h || i < 0 || i >= (int)h->stages.size()) return OCTO_EINVAL;
+  if (name) *name = h->stages[i].name.c_str();
+  if (pairs) *pairs = h->stages[i].pairs;
+  if (cells) *cells = h->stages[i].cells;
+  if (flops) *flops = h->stages[i].flops;
+  if (bytes) *bytes = h->stages[i].bytes;
+  return OCTO_OK;
+}
+
+int octo_fmm_stage_times(octo_fmm_t h, float* ms, int cap) {
+  if (!h || !ms) return OCTO_EINVAL;
+  if (!h->profile) return fail(h, OCTO_ESTATE, "stage profiling is off (option 2)");
+  const int n = (int)h->stages.size();
+  if (cap < n) return fail(h, OCTO_EINVAL, "buffer too small");
+  for (int i = 0; i < n; ++i) {
+    cudaError_t e = cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stage times");
+  }
+  return n;
+}
+
+int octo_fmm_launches_per_solve(octo_fmm_t h) { return h ? count_launches(h) : 0; }
+
+const char* octo_fmm_last_error(octo_fmm_t h) {
+  if (h) return h->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_create_error.c_str();
+}
+
+void octo_fmm_destroy(octo_fmm_t h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Host-side planning of the FMM solve: tree validation, device node order,
+// same-level neighbour tables, per-parity interaction stencils, cross-level pair
+// lists and interaction counts.  Pure C++ (no CUDA calls), so it also runs on a
+// machine without a GPU.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/octo_fmm.h"
+
+namespace octo {
+
+constexpr int kCells = 512;  // 8^3 cells per node
+constexpr int kMaxLevel = 14;
+
+// One stencil entry: a same-level cell offset d (|d_i| <= 7) packed as bytes.
+inline int32_t pack_offset(int dx, int dy, int dz) {
+  return (int32_t)((uint32_t)(uint8_t)(int8_t)dx | ((uint32_t)(uint8_t)(int8_t)dy << 8) |
+                   ((uint32_t)(uint8_t)(int8_t)dz << 16));
+}
+
+struct Plan {
+  // ---- tree in device order (sorted by level, then descriptor order) ----
+  int n_nodes = 0, max_level = 0, n_leaf = 0;
+  std::vector<int32_t> dnode_of_desc;  // descriptor node -> device node
+  std::vector<int32_t> desc_of_dnode;
+  std::vector<int32_t> level, ijk;     // [n], [n*3] in device order
+  std::vector<int32_t> parent, octant; // parent device node, octant in parent
+  std::vector<int32_t> children;       // [n*8] device nodes, -1 for leaves
+  std::vector<int32_t> leaf_id;        // leaf order index (rho/phi/g), -1 for interior
+  std::vector<int32_t> nbr;            // [n*27] same-level neighbour device node or -1
+  std::vector<int32_t> level_start;    // [max_level+2] device-node range per level
+  double origin[3] = {0, 0, 0}, extent = 1.0;
+  double theta = 0.5;
+
+  // ---- stencils (same-level offsets) ----
+  // Level >= 1: 8 parity classes (p = px + 2 py + 4 pz), far offsets whose parent
+  // offset is not far.  Level 0: all far offsets inside [-7, 7]^3.  Near: all
+  // non-zero offsets that are not far (leaf-level P2P).
+  std::vector<int32_t> st_parity;  // [8 * n_st]
+  int n_st = 0;
+  std::vector<int32_t> st_root;
+  std::vector<int32_t> st_near;
+
+  // ---- work lists ----
+  std::vector<int32_t> interior_nodes;   // refined device nodes (all levels)
+  std::vector<int32_t> leaf_nodes;       // leaf device nodes (all levels)
+  std::vector<int32_t> boundary_nodes;   // leaf device nodes with a refined same-level neighbour
+  // cross-level pairs, CSR by target cell (global cell index = dnode*512 + local)
+  std::vector<int64_t> x_targets;        // distinct target cells
+  std::vector<int64_t> x_start;          // [n_targets+1]
+  std::vector<int64_t> x_sources;        // source cell per entry
+
+  // ordered interaction counts: same-level M2L, cross-level M2L, same-level P2P, cross-level P2P
+  int64_t counts[4] = {0, 0, 0, 0};
+  // same-level pairs per kernel: [0] M2L into interior cells, [1] leaf-leaf M2L,
+  // [2] leaf-leaf P2P, [3] M2L from refined neighbours into leaf cells
+  int64_t kernel_pairs[4] = {0, 0, 0, 0};
+
+  std::string error;
+};
+
+// Builds everything above.  Returns OCTO_OK or a negative status (message in plan.error).
+int build_plan(const octo_tree_desc* desc, double theta, Plan& plan);
+
+double cell_width(const Plan& p, int level);
+
+}  // namespace octo

@@ -1,0 +1,165 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by
+element, on the same seeded inputs (float64 path: relative tolerance 1e-12)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_11002_gb300 import binding
+from paper_2304_11002_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def _rel_phi(phi, ref, idx=None):
+    if idx is not None:
+        phi, ref = phi[idx], ref[idx]
+    return float(np.max(np.abs(phi - ref) / np.abs(ref)))
+
+
+def _rel_g(g, ref, idx=None):
+    if idx is not None:
+        g, ref = g[:, idx], ref[:, idx]
+    return float(np.max(np.linalg.norm(g - ref, axis=0)) / np.max(np.linalg.norm(ref, axis=0)))
+
+
+def _run(tree, rho, precision=binding.OCTO_FP64, theta=0.5, graph=True):
+    fmm = binding.OctoFMM(tree, theta, precision)
+    if not graph:
+        binding.octo_fmm_set_option(fmm.handle, 1, 0)
+    r = torch.from_numpy(np.ascontiguousarray(rho.reshape(-1))).cuda()
+    phi, g = fmm.forces(r)
+    torch.cuda.synchronize()
+    return fmm, phi.cpu().numpy(), g.cpu().numpy()
+
+
+def _tiny_adaptive():
+    return W.tree_from_refined({(0, 0, 0, 0), (1, 1, 0, 0)}, 16.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_11002_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_uniform16_fp64_full(seed):
+    w = W.uniform16(seed)
+    fmm, phi, g = _run(w.tree, w.rho)
+    po, go, _ = oracle.fmm(w.tree, w.rho)
+    assert _rel_phi(phi, po) <= TOL64
+    assert _rel_g(g, go) <= TOL64
+
+
+def test_uniform16_multipoles_and_locals():
+    w = W.uniform16(0)
+    fmm, phi, g = _run(w.tree, w.rho)
+    mp = binding.octo_fmm_read_state(fmm.handle, 0, w.tree.n_nodes)
+    mo = oracle.upward(w.tree, w.rho)
+    for f in range(20):
+        s = np.max(np.abs(mo[f])) or 1.0
+        assert np.max(np.abs(mp[f] - mo[f])) <= TOL64 * s, f
+    loc = binding.octo_fmm_read_state(fmm.handle, 1, w.tree.n_nodes)
+    _, _, lo = oracle.fmm(w.tree, w.rho, want_local=True)
+    interior = np.repeat(~w.tree.is_leaf, 512)
+    for f in range(23):
+        a, b = loc[f][interior], lo[f][interior]
+        s = np.max(np.abs(b)) or 1.0
+        assert np.max(np.abs(a - b)) <= TOL64 * s, f
+
+
+def test_tiny_adaptive_fp64_full():
+    tree = _tiny_adaptive()
+    rho = np.random.default_rng(11).lognormal(size=(tree.n_leaf, 512))
+    fmm, phi, g = _run(tree, rho)
+    po, go, _ = oracle.fmm(tree, rho)
+    assert _rel_phi(phi, po) <= TOL64
+    assert _rel_g(g, go) <= TOL64
+
+
+def _sample(n_cells, k, seed):
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(n_cells, size=min(k, n_cells), replace=False))
+    mask = np.zeros(n_cells, dtype=np.uint8)
+    mask[idx] = 1
+    return idx, mask
+
+
+@pytest.mark.parametrize("name", ["adaptive4", "binary64", "adaptive7"])
+def test_sampled_cells_fp64(name):
+    """Full-size trees (64^3 uniform binary; 7-level adaptive binary with ~8000
+    leaf subgrids): every cell computed on the GPU, a seeded sample of cells by
+    the oracle."""
+    w = W.adaptive_binary(3, 0.08) if name == "adaptive4" else W.make(name)
+    fmm, phi, g = _run(w.tree, w.rho)
+    idx, mask = _sample(w.tree.n_leaf * 512, 192, 5)
+    po, go, _ = oracle.fmm(w.tree, w.rho, leaf_mask=mask)
+    assert _rel_phi(phi, po, idx) <= TOL64
+    assert _rel_g(g, go, idx) <= TOL64
+    assert np.all(np.isfinite(phi)) and np.all(np.isfinite(g))
+
+
+def test_counts_from_handle_match_oracle():
+    tree = W.adaptive_binary(3, 0.08).tree
+    fmm = binding.OctoFMM(tree)
+    np.testing.assert_array_equal(fmm.counts(), oracle.counts(tree))
+
+
+def test_homogeneity_and_determinism_bit_exact():
+    w = W.adaptive_binary(3, 0.08)
+    fmm = binding.OctoFMM(w.tree)
+    r = torch.from_numpy(w.rho.reshape(-1).copy()).cuda()
+    phi1, g1 = [x.clone() for x in fmm.forces(r)]
+    phi2, g2 = [x.clone() for x in fmm.forces(r)]
+    phi3, g3 = [x.clone() for x in fmm.forces(2 * r)]
+    assert torch.equal(phi1, phi2) and torch.equal(g1, g2)
+    assert torch.equal(phi3, 2 * phi1) and torch.equal(g3, 2 * g1)
+
+
+def test_graph_and_phases_and_host_path_agree():
+    w = W.adaptive_binary(3, 0.08)
+    fmm = binding.OctoFMM(w.tree)
+    r = torch.from_numpy(w.rho.reshape(-1).copy()).cuda()
+    phi1, g1 = [x.clone() for x in fmm.forces(r)]
+    phi2 = torch.empty_like(phi1)
+    g2 = torch.empty_like(g1)
+    binding.octo_fmm_upward(fmm.handle, r)
+    binding.octo_fmm_interact(fmm.handle)
+    binding.octo_fmm_downward(fmm.handle, phi2, g2)
+    torch.cuda.synchronize()
+    assert torch.equal(phi1, phi2) and torch.equal(g1, g2)
+    rho_h = w.rho.reshape(-1).copy()
+    phi_h = np.empty_like(rho_h)
+    g_h = np.empty((3, rho_h.size))
+    binding.octo_fmm_forces_host(fmm.handle, rho_h, phi_h, g_h)
+    assert np.array_equal(phi_h, phi1.cpu().numpy()) and np.array_equal(g_h, g1.cpu().numpy())
+
+
+def test_conservation_on_gpu_output():
+    """Newton III and angular momentum (Section IV-C) hold for the GPU forces."""
+    tree = _tiny_adaptive()
+    rho = np.random.default_rng(12).lognormal(size=(tree.n_leaf, 512))
+    _, phi, g = _run(tree, rho)
+    m = rho.reshape(-1) * tree.leaf_cell_h() ** 3
+    x = tree.leaf_cell_centres()
+    F = (m[None, :] * g).T
+    assert np.linalg.norm(F.sum(0)) <= 1e-13 * np.abs(F).sum()
+    tau = np.cross(x, F)
+    assert np.linalg.norm(tau.sum(0)) <= 1e-13 * np.abs(tau).sum()
+
+
+def test_errors_are_reported():
+    w = W.uniform16(0)
+    with pytest.raises(binding.OctoError) as e:
+        binding.octo_fmm_create(w.tree, 0.5, 4, binding.OCTO_FP64)
+    assert e.value.code == -1
+    fmm = binding.OctoFMM(w.tree)
+    d = torch.empty(4096, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.OctoError) as e:
+        binding.octo_fmm_backward(fmm.handle, d, torch.empty((3, 4096), dtype=torch.float64, device="cuda"), d)
+    assert e.value.code == -7
