@@ -180,3 +180,34 @@ def l2l(parent, delta) -> np.ndarray:
     out = np.empty(23)
     lib().oracle_l2l(_p(P, _dp), _p(d, _dp), _p(out, _dp))
     return out
+
+
+def fmm_vjp(tree, rho, phib, gb, theta: float = 0.5, correction: bool = True) -> np.ndarray:
+    """drho = (dphi/drho)^T phib + (dg/drho)^T gb (reverse of every step of the solve)."""
+    ta = _TreeArgs(tree)
+    L = lib()
+    if not getattr(L, "_vjp_typed", False):
+        L.oracle_fmm_vjp.argtypes = [ctypes.c_int, _ip, _ip, _ip, _dp, ctypes.c_double, _dp, ctypes.c_double,
+                                     ctypes.c_int, _dp, _dp, _dp]
+        L.oracle_fmm_vjp.restype = ctypes.c_int
+        L.oracle_dtensor5.argtypes = [_dp, _dp]
+        L.oracle_dtensor5.restype = None
+        L._vjp_typed = True
+    rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+    phib = np.ascontiguousarray(phib, dtype=np.float64).reshape(-1)
+    gb = np.ascontiguousarray(gb, dtype=np.float64).reshape(3, -1)
+    out = np.empty_like(rho)
+    _check(L.oracle_fmm_vjp(*ta.args(), _p(rho, _dp), float(theta), 1 if correction else 0, _p(phib, _dp),
+                            _p(gb, _dp), _p(out, _dp)), "fmm_vjp")
+    return out
+
+
+def dtensor5(R) -> np.ndarray:
+    fmm_vjp  # ensure argtypes are set by a first call path
+    L = lib()
+    L.oracle_dtensor5.argtypes = [_dp, _dp]
+    L.oracle_dtensor5.restype = None
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    out = np.empty(243)
+    L.oracle_dtensor5(_p(R, _dp), _p(out, _dp))
+    return out.reshape(3, 3, 3, 3, 3)

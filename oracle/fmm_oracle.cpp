@@ -554,6 +554,219 @@ void leaf_outputs(const Tree& t, const vector<char>& need, const vector<Loc<T>>&
   }
 }
 
+// ---------------------------------------------------------------------------
+// Vector-Jacobian product (reverse of every step above, float64, full tensors).
+// ---------------------------------------------------------------------------
+
+// D^(5) = grad^5 (1/|R|) from the expansion of derivatives of a radial function:
+// for the multi-index with exponents (a, b, c),
+//   d^a_x d^b_y d^c_z F(r) = sum_{i,j,k} H(a,i) H(b,j) H(c,k) x^(a-2i) y^(b-2j) z^(c-2k) F_{n-i-j-k},
+//   H(a,i) = a! / (2^i i! (a-2i)!),  F_m = (r^-1 d/dr)^m (1/r) = (-1)^m (2m-1)!! r^-(2m+1).
+double hermite_coef(int a, int i) {
+  double f = 1;
+  for (int k = 2; k <= a; ++k) f *= k;
+  double d = std::ldexp(1.0, i);
+  for (int k = 2; k <= i; ++k) d *= k;
+  for (int k = 2; k <= a - 2 * i; ++k) d *= k;
+  return f / d;
+}
+
+void derivative5(const double R[3], double D5[3][3][3][3][3]) {
+  double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+  double F[6];
+  F[0] = 1.0 / std::sqrt(r2);
+  for (int m = 1; m < 6; ++m) F[m] = -(2.0 * m - 1.0) * F[m - 1] / r2;
+  double pw[3][6];
+  for (int d = 0; d < 3; ++d) {
+    pw[d][0] = 1.0;
+    for (int k = 1; k < 6; ++k) pw[d][k] = pw[d][k - 1] * R[d];
+  }
+  double byexp[6][6];  // [a][b], c = 5 - a - b
+  for (int a = 0; a <= 5; ++a)
+    for (int b = 0; a + b <= 5; ++b) {
+      int c = 5 - a - b;
+      double s = 0;
+      for (int i = 0; 2 * i <= a; ++i)
+        for (int j = 0; 2 * j <= b; ++j)
+          for (int k = 0; 2 * k <= c; ++k)
+            s += hermite_coef(a, i) * hermite_coef(b, j) * hermite_coef(c, k) * pw[0][a - 2 * i] * pw[1][b - 2 * j] *
+                 pw[2][c - 2 * k] * F[5 - i - j - k];
+      byexp[a][b] = s;
+    }
+  for (int i0 = 0; i0 < 3; ++i0)
+    for (int i1 = 0; i1 < 3; ++i1)
+      for (int i2 = 0; i2 < 3; ++i2)
+        for (int i3 = 0; i3 < 3; ++i3)
+          for (int i4 = 0; i4 < 3; ++i4) {
+            int e[3] = {0, 0, 0};
+            e[i0]++, e[i1]++, e[i2]++, e[i3]++, e[i4]++;
+            D5[i0][i1][i2][i3][i4] = byexp[e[0]][e[1]];
+          }
+}
+
+// Adjoint of the M2L of B into A (see m2l): given Lb = dS/dL_A (and dS/d dg_A in
+// Lb.dg), adds dS/d(multipole of A) into Ab and dS/d(multipole of B) into Bb.
+void m2l_vjp(const Mp<double>& A, const Mp<double>& B, const Loc<double>& Lb, bool correction, Mp<double>& Ab,
+             Mp<double>& Bb) {
+  double R[3];
+  for (int a = 0; a < 3; ++a) R[a] = A.X[a] - B.X[a];
+  DT<double> D;
+  derivative_tensors(R, D);
+  static thread_local double D5[3][3][3][3][3];
+  derivative5(R, D5);
+  // adjoints of the derivative tensors
+  double D0b = -B.m * Lb.L0, D1b[3], D2b[3][3], D3b[3][3][3], D4b[3][3][3][3];
+  for (int a = 0; a < 3; ++a) {
+    D1b[a] = -B.m * Lb.L1[a];
+    for (int b = 0; b < 3; ++b) {
+      D2b[a][b] = -0.5 * Lb.L0 * B.M2[a][b] - B.m * Lb.L2[a][b];
+      for (int c = 0; c < 3; ++c) {
+        D3b[a][b][c] = Lb.L0 * B.M3[a][b][c] / 6.0 - 0.5 * Lb.L1[a] * B.M2[b][c] - B.m * Lb.L3[a][b][c];
+        for (int e = 0; e < 3; ++e)
+          D4b[a][b][c][e] = correction ? Lb.dg[a] * (B.m * A.M3[b][c][e] - A.m * B.M3[b][c][e]) / (6.0 * A.m) : 0.0;
+      }
+    }
+  }
+  // multipole adjoints
+  double mB = -Lb.L0 * D.D0;
+  for (int a = 0; a < 3; ++a) {
+    mB -= Lb.L1[a] * D.D1[a];
+    for (int b = 0; b < 3; ++b) {
+      mB -= Lb.L2[a][b] * D.D2[a][b];
+      for (int c = 0; c < 3; ++c) mB -= Lb.L3[a][b][c] * D.D3[a][b][c];
+    }
+  }
+  for (int b = 0; b < 3; ++b)
+    for (int c = 0; c < 3; ++c) {
+      double s = Lb.L0 * D.D2[b][c];
+      for (int a = 0; a < 3; ++a) s += Lb.L1[a] * D.D3[a][b][c];
+      Bb.M2[b][c] += -0.5 * s;
+    }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) Bb.M3[a][b][c] += Lb.L0 * D.D3[a][b][c] / 6.0;
+  if (correction) {
+    double mA = 0;
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c)
+        for (int e = 0; e < 3; ++e) {
+          double t = 0;  // sum_a dg_a D4_abce
+          for (int a = 0; a < 3; ++a) t += Lb.dg[a] * D.D4[a][b][c][e];
+          mB += t * A.M3[b][c][e] / (6.0 * A.m);
+          Bb.M3[b][c][e] += -t / 6.0;
+          Ab.M3[b][c][e] += B.m * t / (6.0 * A.m);
+          mA += -B.m * t * A.M3[b][c][e] / (6.0 * A.m * A.m);
+        }
+    Ab.m += mA;
+  }
+  Bb.m += mB;
+  // position adjoints through R = X_A - X_B
+  for (int f = 0; f < 3; ++f) {
+    double s = D0b * D.D1[f];
+    for (int a = 0; a < 3; ++a) {
+      s += D1b[a] * D.D2[a][f];
+      for (int b = 0; b < 3; ++b) {
+        s += D2b[a][b] * D.D3[a][b][f];
+        for (int c = 0; c < 3; ++c) {
+          s += D3b[a][b][c] * D.D4[a][b][c][f];
+          for (int e = 0; e < 3; ++e) s += D4b[a][b][c][e] * D5[a][b][c][e][f];
+        }
+      }
+    }
+    Ab.X[f] += s;
+    Bb.X[f] -= s;
+  }
+}
+
+// Adjoint of the P2P of leaf cell B into leaf cell A (positions are fixed).
+void p2p_vjp(const Mp<double>& A, const Mp<double>& B, double phib, const double* gb, Mp<double>& Bb) {
+  double R[3];
+  for (int a = 0; a < 3; ++a) R[a] = A.X[a] - B.X[a];
+  double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+  double r = std::sqrt(r2);
+  double s = -phib / r;
+  for (int a = 0; a < 3; ++a) s += -gb[a] * R[a] / (r2 * r);
+  Bb.m += s;
+}
+
+// Adjoint of the Taylor shift (l2l): given Cb = dS/dC (C the child's expansion),
+// adds into Pb = dS/dP and returns dS/d delta in db.
+void l2l_vjp(const Loc<double>& P, const double d[3], const Loc<double>& Cb, Loc<double>& Pb, double db[3]) {
+  Pb.L0 += Cb.L0;
+  for (int a = 0; a < 3; ++a) {
+    Pb.L1[a] += Cb.L0 * d[a] + Cb.L1[a];
+    Pb.dg[a] += Cb.dg[a];
+    for (int b = 0; b < 3; ++b) {
+      Pb.L2[a][b] += 0.5 * Cb.L0 * d[a] * d[b] + Cb.L1[a] * d[b] + Cb.L2[a][b];
+      for (int c = 0; c < 3; ++c)
+        Pb.L3[a][b][c] += Cb.L0 * d[a] * d[b] * d[c] / 6.0 + 0.5 * Cb.L1[a] * d[b] * d[c] + Cb.L2[a][b] * d[c] +
+                          Cb.L3[a][b][c];
+    }
+  }
+  // S = Cb . shift(P, d); differentiate every d factor
+  for (int f = 0; f < 3; ++f) {
+    double s = 0;
+    // from L0' = L0 + L1.d + L2:dd/2 + L3:ddd/6
+    s += Cb.L0 * P.L1[f];
+    for (int a = 0; a < 3; ++a) {
+      s += Cb.L0 * 0.5 * (P.L2[f][a] + P.L2[a][f]) * d[a];
+      for (int b = 0; b < 3; ++b)
+        s += Cb.L0 * (P.L3[f][a][b] + P.L3[a][f][b] + P.L3[a][b][f]) * d[a] * d[b] / 6.0;
+    }
+    // from L1'_a = L1_a + L2_ab d_b + L3_abc d_b d_c / 2
+    for (int a = 0; a < 3; ++a) {
+      s += Cb.L1[a] * P.L2[a][f];
+      for (int b = 0; b < 3; ++b) s += Cb.L1[a] * 0.5 * (P.L3[a][f][b] + P.L3[a][b][f]) * d[b];
+    }
+    // from L2'_ab = L2_ab + L3_abc d_c
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) s += Cb.L2[a][b] * P.L3[a][b][f];
+    db[f] = s;
+  }
+}
+
+// Adjoint of m2m: given Pb = dS/dP, adds dS/d(child) into chb[i].
+void m2m_vjp(const Mp<double>* ch, int nch, const Mp<double>& P, const Mp<double>& Pb, Mp<double>* chb) {
+  double Xb[3] = {Pb.X[0], Pb.X[1], Pb.X[2]};  // grows with the d_c = X_c - X_P terms
+  for (int i = 0; i < nch; ++i) {
+    const Mp<double>& c = ch[i];
+    double d[3], db[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) d[a] = c.X[a] - P.X[a];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        // M2_P,ab += M2_c,ab + m d_a d_b
+        chb[i].M2[a][b] += Pb.M2[a][b];
+        chb[i].m += Pb.M2[a][b] * d[a] * d[b];
+        db[a] += Pb.M2[a][b] * c.m * d[b];
+        db[b] += Pb.M2[a][b] * c.m * d[a];
+        for (int e = 0; e < 3; ++e) {
+          // M3_P,abe += M3_c + M2_ab d_e + M2_ae d_b + M2_be d_a + m d_a d_b d_e
+          double w = Pb.M3[a][b][e];
+          chb[i].M3[a][b][e] += w;
+          chb[i].M2[a][b] += w * d[e];
+          chb[i].M2[a][e] += w * d[b];
+          chb[i].M2[b][e] += w * d[a];
+          chb[i].m += w * d[a] * d[b] * d[e];
+          db[e] += w * (c.M2[a][b] + c.m * d[a] * d[b]);
+          db[b] += w * (c.M2[a][e] + c.m * d[a] * d[e]);
+          db[a] += w * (c.M2[b][e] + c.m * d[b] * d[e]);
+        }
+      }
+    for (int a = 0; a < 3; ++a) {
+      chb[i].X[a] += db[a];
+      Xb[a] -= db[a];
+    }
+  }
+  // X_P = sum m_c X_c / m_P and m_P = sum m_c
+  for (int i = 0; i < nch; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      chb[i].X[a] += Xb[a] * ch[i].m / P.m;
+      chb[i].m += Xb[a] * (ch[i].X[a] - P.X[a]) / P.m;
+    }
+    chb[i].m += Pb.m;
+  }
+}
+
 // Packed orders shared by the exported arrays (documented in oracle/__init__.py):
 // multipole: m, X0..2, M2 {00,01,02,11,12,22}, M3 {000,001,002,011,012,022,111,112,122,222}
 // local:     L0, L1 0..2, L2 {..6}, L3 {..10}, dg 0..2
@@ -827,6 +1040,159 @@ void oracle_l2l(const double* parent, const double* delta, double* out) {
   zero(C);
   l2l(P, delta, C);
   pack_loc(C, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// drho = J^T (dphi, dg) of the full solve, by the reverse of each step:
+// L2P^T seeds, L2L^T (finest to coarsest), M2L^T / P2P^T over every ordered pair,
+// M2M^T (coarsest to finest), P2M^T.
+int fmm_vjp(const Tree& t, const double* rho, double theta, bool corr, const double* phib, const double* gb,
+            double* rhob) {
+  Solver<double> s(t, theta, corr);
+  s.upward(rho);
+  const size_t NC = s.mp.size();
+  vector<char> all(NC, 1);
+  vector<Loc<double>> L;
+  vector<double> pphi, pg;
+  s.interact_down(all, L, pphi, pg);  // final local expansions of every cell
+  struct Pr {
+    int64_t tgt, src;
+    int kind;
+  };
+  vector<Pr> prs;
+  auto visit = [&](int64_t A, int64_t B, int kind) {
+    prs.push_back({A, B, kind});
+    prs.push_back({B, A, kind});
+  };
+  Walker<decltype(visit)> w{t, theta, nullptr, visit};
+  w.run();
+  // seeds at leaf cells: phi = L0 + P2P, g = -L1 + dg + P2P
+  vector<Loc<double>> Lb(NC);
+  for (auto& x : Lb) zero(x);
+  vector<double> pphib(NC, 0.0), pgb(3 * NC, 0.0);
+  const size_t nl = (size_t)t.n_leaf * 512;
+  for (int nd = 0; nd < t.n; ++nd) {
+    if (!t.is_leaf(nd)) continue;
+    for (int l = 0; l < 512; ++l) {
+      size_t id = (size_t)nd * 512 + l, k = (size_t)t.leaf_id[nd] * 512 + l;
+      Lb[id].L0 = phib[k];
+      pphib[id] = phib[k];
+      for (int a = 0; a < 3; ++a) {
+        Lb[id].L1[a] = -gb[a * nl + k];
+        Lb[id].dg[a] = gb[a * nl + k];
+        pgb[3 * id + a] = gb[a * nl + k];
+      }
+    }
+  }
+  vector<Mp<double>> mpb(NC);
+  for (auto& x : mpb) zero(x);
+  // L2L^T
+  for (int lv = t.max_level; lv >= 1; --lv)
+    for (int nd = 0; nd < t.n; ++nd) {
+      if (t.level[nd] != lv) continue;
+      for (int l = 0; l < 512; ++l) {
+        int64_t c = (int64_t)nd * 512 + l, p = parent_cell(t, c);
+        double d[3], db[3];
+        for (int a = 0; a < 3; ++a) d[a] = s.mp[c].X[a] - s.mp[p].X[a];
+        l2l_vjp(L[p], d, Lb[c], Lb[p], db);
+        for (int a = 0; a < 3; ++a) {
+          mpb[c].X[a] += db[a];
+          mpb[p].X[a] -= db[a];
+        }
+      }
+    }
+  // M2L^T and P2P^T: target-side gradients grouped by target, source-side by source
+  for (int side = 0; side < 2; ++side) {
+    std::stable_sort(prs.begin(), prs.end(), [&](const Pr& a, const Pr& b) {
+      return side == 0 ? a.tgt < b.tgt : a.src < b.src;
+    });
+    vector<size_t> start;
+    for (size_t i = 0; i < prs.size(); ++i)
+      if (i == 0 || (side == 0 ? prs[i].tgt != prs[i - 1].tgt : prs[i].src != prs[i - 1].src)) start.push_back(i);
+    start.push_back(prs.size());
+    const long ngroups = (long)start.size() - 1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long g = 0; g < ngroups; ++g) {
+      for (size_t i = start[g]; i < start[g + 1]; ++i) {
+        const Pr& pr = prs[i];
+        Mp<double> Ab, Bb;
+        zero(Ab);
+        zero(Bb);
+        if (pr.kind == 0)
+          m2l_vjp(s.mp[pr.tgt], s.mp[pr.src], Lb[pr.tgt], corr, Ab, Bb);
+        else if (side == 1)
+          p2p_vjp(s.mp[pr.tgt], s.mp[pr.src], pphib[pr.tgt], &pgb[3 * pr.tgt], Bb);
+        Mp<double>& dst = side == 0 ? mpb[pr.tgt] : mpb[pr.src];
+        const Mp<double>& v = side == 0 ? Ab : Bb;
+        dst.m += v.m;
+        for (int a = 0; a < 3; ++a) {
+          dst.X[a] += v.X[a];
+          for (int b = 0; b < 3; ++b) {
+            dst.M2[a][b] += v.M2[a][b];
+            for (int c = 0; c < 3; ++c) dst.M3[a][b][c] += v.M3[a][b][c];
+          }
+        }
+      }
+    }
+  }
+  // M2M^T, coarsest to finest
+  for (int lv = 0; lv < t.max_level; ++lv)
+    for (int nd = 0; nd < t.n; ++nd) {
+      if (t.level[nd] != lv || t.is_leaf(nd)) continue;
+      for (int l = 0; l < 512; ++l) {
+        int64_t id = (int64_t)nd * 512 + l, ch[8];
+        child_cells(t, id, ch);
+        Mp<double> c[8], cb[8];
+        for (int i = 0; i < 8; ++i) {
+          c[i] = s.mp[ch[i]];
+          zero(cb[i]);
+        }
+        m2m_vjp(c, 8, s.mp[id], mpb[id], cb);
+        for (int i = 0; i < 8; ++i) {
+          Mp<double>& dst = mpb[ch[i]];
+          dst.m += cb[i].m;
+          for (int a = 0; a < 3; ++a) {
+            dst.X[a] += cb[i].X[a];
+            for (int b = 0; b < 3; ++b) {
+              dst.M2[a][b] += cb[i].M2[a][b];
+              for (int e = 0; e < 3; ++e) dst.M3[a][b][e] += cb[i].M3[a][b][e];
+            }
+          }
+        }
+      }
+    }
+  // P2M^T: m = rho h^3 (leaf positions and zero higher moments are constants)
+  for (int nd = 0; nd < t.n; ++nd) {
+    if (!t.is_leaf(nd)) continue;
+    double h = t.h(t.level[nd]);
+    for (int l = 0; l < 512; ++l)
+      rhob[(size_t)t.leaf_id[nd] * 512 + l] = mpb[(size_t)nd * 512 + l].m * (h * h * h);
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Vector-Jacobian product of the full solve: drho = (dphi/drho)^T phib + (dg/drho)^T gb.
+int oracle_fmm_vjp(int n, const int32_t* level, const int32_t* ijk, const int32_t* children, const double* origin,
+                   double extent, const double* rho, double theta, int flags, const double* phib, const double* gb,
+                   double* rhob) {
+  Tree t;
+  int rc = build_tree(t, n, level, ijk, children, origin, extent);
+  if (rc) return rc;
+  return fmm_vjp(t, rho, theta, flags & 1, phib, gb, rhob);
+}
+
+// D^(5) (243 values, row-major) for the pins.
+void oracle_dtensor5(const double* R, double* out) {
+  double D5[3][3][3][3][3];
+  derivative5(R, D5);
+  std::memcpy(out, D5, sizeof(D5));
 }
 
 }  // extern "C"
