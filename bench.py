@@ -280,8 +280,11 @@ def run_ours(args):
     fp64 = None
     if precision == binding.OCTO_MIXED and not args.no_fp64:
         del fmm
-        _, _, s_ms, _, _, _ = time_solver(w, binding.OCTO_FP64, max(2, args.steps // 2), 1, torch, flush, stream)
-        fp64 = {"value": n_inter / (float(np.mean(s_ms)) / 1e3), "ms_per_step": float(np.mean(s_ms))}
+        _, info64, s_ms, st_ms, _, _ = time_solver(w, binding.OCTO_FP64, max(3, args.steps // 2), 3, torch, flush,
+                                                   stream)
+        m64 = st_ms.mean(axis=0)
+        fp64 = {"value": n_inter / (float(np.mean(s_ms)) / 1e3), "ms_per_step": float(np.mean(s_ms)),
+                "stages_ms": {info64[i]["name"]: round(float(m64[i]), 4) for i in range(len(info64))}}
 
     if rank != 0:
         return 0

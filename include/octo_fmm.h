@@ -129,11 +129,26 @@ int octo_fmm_plan_counts(const octo_tree_desc* tree, double theta, int64_t count
  * Synchronises the device. */
 int octo_fmm_read_state(octo_fmm_t h, int which, double* host_out);
 
-/* Options: key 0 = stencil chunks per interior subgrid (0 = autotune), key 1 =
- * replay the whole solve from a captured CUDA graph (1, default) or launch the
- * stages one by one (0), key 2 = record per-stage timing events (1/0, default 0).
- * Returns OCTO_EINVAL for an unknown key or value. */
+/* Options:
+ *  key 1: replay the whole solve from a captured CUDA graph (1, default) or launch
+ *         the stages one by one (0);
+ *  key 2: record per-stage timing events inside the graph (1/0, default 0);
+ *  key 3: strategy of the batched interaction phase (Section VII-C's same-level
+ *         interactions of every level in one phase): 0 = autotune on the first
+ *         forces call (default; times the candidates on this tree and keeps the
+ *         fastest), 1 = one launch per item kind over all levels, 2 = one
+ *         persistent launch pulling interior and leaf items of every level from a
+ *         work queue;
+ *  key 4: register budget of the persistent launch: 1 or 2 resident blocks per SM.
+ * Setting an option drops the captured graph.  Returns OCTO_EINVAL for an unknown
+ * key or value. */
 int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value);
+
+/* Reads an option (keys 1-4 above; key 3 reports the strategy in use after
+ * autotuning) or an autotuner measurement: keys 10, 11, 12 = mean interaction
+ * time in microseconds of per-kind launches, persistent (1 block/SM budget) and
+ * persistent (2 blocks/SM budget); 0 before autotuning. */
+int octo_fmm_get_option(octo_fmm_t h, int key, int64_t* value);
 
 /* Number of kernel launches one octo_fmm_forces call enqueues. */
 int octo_fmm_launches_per_solve(octo_fmm_t h);

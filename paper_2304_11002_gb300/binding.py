@@ -26,7 +26,8 @@ STATUS = {0: "OCTO_OK", -1: "OCTO_EINVAL", -2: "OCTO_ETREE", -3: "OCTO_ENOMEM", 
 # every symbol include/octo_fmm.h declares
 SYMBOLS = ["octo_fmm_create", "octo_fmm_upward", "octo_fmm_interact", "octo_fmm_downward", "octo_fmm_forces",
            "octo_fmm_forces_host", "octo_fmm_backward", "octo_fmm_stats", "octo_fmm_plan_counts",
-           "octo_fmm_read_state", "octo_fmm_set_option", "octo_fmm_launches_per_solve", "octo_fmm_stage_count",
+           "octo_fmm_read_state", "octo_fmm_set_option", "octo_fmm_get_option", "octo_fmm_launches_per_solve",
+           "octo_fmm_stage_count",
            "octo_fmm_stage_info", "octo_fmm_stage_times", "octo_fmm_last_error", "octo_fmm_destroy"]
 
 
@@ -64,6 +65,7 @@ def lib() -> ctypes.CDLL:
         L.octo_fmm_plan_counts.argtypes = [ctypes.POINTER(TreeDesc), ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]
         L.octo_fmm_read_state.argtypes = [vp, ctypes.c_int, dp]
         L.octo_fmm_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
+        L.octo_fmm_get_option.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
         L.octo_fmm_launches_per_solve.argtypes = [vp]
         L.octo_fmm_stage_count.argtypes = [vp]
         i64p = ctypes.POINTER(ctypes.c_int64)
@@ -175,6 +177,12 @@ def octo_fmm_read_state(h, which: int, n_nodes: int) -> np.ndarray:
 
 def octo_fmm_set_option(h, key: int, value: int) -> None:
     _check(lib().octo_fmm_set_option(h, int(key), int(value)), h)
+
+
+def octo_fmm_get_option(h, key: int) -> int:
+    v = ctypes.c_int64()
+    _check(lib().octo_fmm_get_option(h, int(key), ctypes.byref(v)), h)
+    return int(v.value)
 
 
 def octo_fmm_launches_per_solve(h) -> int:

@@ -20,7 +20,8 @@ BUILD = os.path.join(HERE, "_lib", "obj")
 LIB = os.path.join(HERE, "_lib", "liboctofmm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["capi.cu", "kernels_fp64.cu", "kernels_mixed.cu"]
+CU_SOURCES = ["capi.cu", "kernels_fp64.cu", "kernels_mixed.cu", "kernels_adjoint.cu", "kernels_boundary.cu",
+              "kernels_interact.cu"]
 CXX_SOURCES = ["plan.cpp"]
 
 
@@ -56,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
-    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC]
+    common = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-I", INC]
     jobs = []
     for f in CU_SOURCES:
         obj = os.path.join(BUILD, f + ".o")

@@ -45,6 +45,21 @@ struct octo_fmm {
   Kappa* d_kappa = nullptr;
   int64_t *d_xf_t = nullptr, *d_xf_s = nullptr, *d_xf_src = nullptr;
   int64_t *d_xl_t = nullptr, *d_xl_s = nullptr, *d_xl_src = nullptr;
+  int64_t *d_xf_m = nullptr, *d_xl_m = nullptr;
+  // batched interaction phase: strategy (MODE_*), persistent work queue and counter
+  int mode = 0, requested_mode = 0;
+  int min_blocks = 1, n_sm = 0;
+  int persist_per_sm[3] = {0, 0, 0};  // resident blocks per SM of the persistent variants (index = budget)
+  int* d_queue = nullptr;
+  int n_items = 0;
+  int* d_counter = nullptr;
+  int* d_err = nullptr;  // device-side check word of the adjoint kernels
+  float tune_ms[3] = {0, 0, 0};  // measured interaction time per strategy (autotune)
+  double *d_mpb = nullptr, *d_locb = nullptr;  // adjoint workspace
+  int* d_general = nullptr;
+  int n_general = 0;
+  int *d_st_slot = nullptr, *d_st_slot_off = nullptr;
+  int64_t xf_p2p = 0, xl_p2p = 0;  // near (P2P) entries of the cross-level lists
   int n_xf = 0, n_xl = 0;
   int64_t xf_pairs = 0, xl_pairs = 0;
 
@@ -100,6 +115,8 @@ void free_all(octo_fmm* h) {
                   h->d_ijk,      h->d_interior, h->d_leaf,  h->d_boundary, h->d_st_parity, h->d_st_root,
                   h->d_st_near,  h->d_kappa,   h->d_xf_t,   h->d_xf_s,     h->d_xf_src,  h->d_xl_t,
                   h->d_xl_s,     h->d_xl_src,  h->d_mp,     h->d_loc,      h->d_io,        h->d_mp32,
+                  h->d_xf_m,     h->d_xl_m,    h->d_st_slot, h->d_st_slot_off, h->d_mpb, h->d_locb,
+                  h->d_general,  h->d_queue,   h->d_counter, h->d_err,
                   h->d_kappa32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -110,7 +127,11 @@ void free_all(octo_fmm* h) {
     if (ev) cudaEventDestroy(ev);
 }
 
-enum StageKind { S_P2M, S_M2M, S_M2L, S_CONV, S_BOUNDARY, S_CROSS_FULL, S_CROSS_LEAF, S_L2L };
+// Kinds in solve order; [S_M2L, S_CROSS_LEAF] is the interaction phase.
+enum StageKind { S_P2M, S_M2M, S_M2L, S_CONV, S_PERSIST, S_CROSS_FULL, S_CROSS_LEAF, S_L2L };
+
+// Interaction strategies (option key 3).
+enum { MODE_AUTO = 0, MODE_PER_KIND = 1, MODE_PERSISTENT = 2 };
 
 // Floating-point operations of the per-pair expression as written (a fused
 // multiply-add counts as two), obtained by running the same template with a
@@ -148,6 +169,8 @@ int64_t m2l_pair_flops() {
   return g_counted_ops + 3 + 5 + 8;
 }
 constexpr int64_t kConvFlopsPerPair = 8;  // four fused multiply-adds
+// exact point-mass pair: R (3), r^2 (5), reciprocal square root (8), m/r, m/r^3 (3), phi and g (7)
+constexpr int64_t kP2PFlopsPerPair = 26;
 
 // Builds the fixed stage list (its length does not depend on the data, so the
 // whole sequence can be captured once into a CUDA graph).
@@ -160,10 +183,15 @@ void make_stages(octo_fmm* h) {
       case S_P2M: bytes = cells * 16; break;                      // rho in, m out
       case S_M2M: bytes = cells * (8 * 20 + 20) * 8; break;        // 8 children in, parent out
       case S_M2L: flops = pairs * m2l_pair_flops<true, true>(); break;
-      case S_CONV: flops = pairs * kConvFlopsPerPair; break;
-      case S_BOUNDARY: flops = pairs * m2l_pair_flops<false, false>(); break;
-      case S_CROSS_FULL: flops = pairs * m2l_pair_flops<true, true>(); break;
-      case S_CROSS_LEAF: flops = pairs * m2l_pair_flops<false, false>(); break;
+      case S_CONV:
+        flops = (pairs - P.kernel_pairs[3]) * kConvFlopsPerPair + P.kernel_pairs[3] * m2l_pair_flops<false, false>();
+        break;
+      case S_PERSIST:
+        flops = P.kernel_pairs[0] * m2l_pair_flops<true, true>() + (P.kernel_pairs[1] + P.kernel_pairs[2]) * kConvFlopsPerPair +
+                P.kernel_pairs[3] * m2l_pair_flops<false, false>();
+        break;
+      case S_CROSS_FULL: flops = (pairs - h->xf_p2p) * m2l_pair_flops<true, true>() + h->xf_p2p * kP2PFlopsPerPair; break;
+      case S_CROSS_LEAF: flops = (pairs - h->xl_p2p) * m2l_pair_flops<false, false>() + h->xl_p2p * kP2PFlopsPerPair; break;
       case S_L2L: bytes = cells * 52 * 8; break;                   // own L/X in + L out + parent share
     }
     h->stages.push_back({kind, a, b, std::move(name), pairs, cells, flops, bytes});
@@ -176,14 +204,18 @@ void make_stages(octo_fmm* h) {
       for (int k = P.level_start[l]; k < P.level_start[l + 1]; ++k) ni += P.children[8 * k] >= 0;
       add(S_M2M, P.level_start[l], P.level_start[l + 1], "m2m_l" + std::to_string(l), 0, ni * kCells);
     }
-  if (!P.interior_nodes.empty())
-    add(S_M2L, 0, 0, h->precision == OCTO_MIXED ? "m2l_interior_f32" : "m2l_interior", P.kernel_pairs[0],
-        (int64_t)P.interior_nodes.size() * kCells);
-  if (!P.leaf_nodes.empty())
-    add(S_CONV, 0, 0, h->precision == OCTO_MIXED ? "leaf_conv_mixed" : "leaf_conv",
-        P.kernel_pairs[1] + P.kernel_pairs[2], (int64_t)P.leaf_nodes.size() * kCells);
-  if (!P.boundary_nodes.empty())
-    add(S_BOUNDARY, 0, 0, "m2l_boundary", P.kernel_pairs[3], (int64_t)P.boundary_nodes.size() * kCells);
+  const bool mixed = h->precision == OCTO_MIXED;
+  if (h->mode == MODE_PERSISTENT) {
+    add(S_PERSIST, 0, 0, mixed ? "interact_persistent_mixed" : "interact_persistent",
+        P.kernel_pairs[0] + P.kernel_pairs[1] + P.kernel_pairs[2] + P.kernel_pairs[3], (int64_t)P.n_nodes * kCells);
+  } else {
+    if (!P.interior_nodes.empty())
+      add(S_M2L, 0, 0, mixed ? "m2l_interior_f32" : "m2l_interior", P.kernel_pairs[0],
+          (int64_t)P.interior_nodes.size() * kCells);
+    if (!P.leaf_nodes.empty())
+      add(S_CONV, 0, 0, mixed ? "leaf_mixed" : "leaf", P.kernel_pairs[1] + P.kernel_pairs[2] + P.kernel_pairs[3],
+          (int64_t)P.leaf_nodes.size() * kCells);
+  }
   if (h->n_xf > 0) add(S_CROSS_FULL, 0, 0, "cross_interior", h->xf_pairs, h->n_xf);
   if (h->n_xl > 0) add(S_CROSS_LEAF, 0, 0, "cross_leaf", h->xl_pairs, h->n_xl);
   for (int l = 0; l <= P.max_level; ++l)
@@ -192,25 +224,56 @@ void make_stages(octo_fmm* h) {
           (int64_t)(P.level_start[l + 1] - P.level_start[l]) * kCells);
 }
 
+// Rebuilds the stage list for the current strategy, with one timing event per
+// stage boundary, and drops the captured graph.
+cudaError_t rebuild_stages(octo_fmm* h) {
+  make_stages(h);
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  while (h->ev.size() < h->stages.size() + 1) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    h->ev.push_back(ev);
+  }
+  return cudaSuccess;
+}
+
+InteractArgs interact_args(const octo_fmm* h) {
+  const Plan& P = h->plan;
+  InteractArgs a;
+  a.mp = h->d_mp;
+  a.mp32 = h->d_mp32;
+  a.loc = h->d_loc;
+  a.st = h->st;
+  a.mixed = h->precision == OCTO_MIXED;
+  a.interior = h->d_interior;
+  a.n_interior = (int)P.interior_nodes.size();
+  a.leaf = h->d_leaf;
+  a.n_leaf = (int)P.leaf_nodes.size();
+  a.queue = h->d_queue;
+  a.n_items = h->n_items;
+  a.counter = h->d_counter;
+  a.grid = h->n_sm * h->persist_per_sm[h->min_blocks];
+  a.min_blocks = h->min_blocks;
+  return a;
+}
+
 cudaError_t enq_stage(octo_fmm* h, const octo_fmm::Stage& st, const double* rho, double* phi, double* g,
                       cudaStream_t s) {
   const Plan& P = h->plan;
   switch (st.kind) {
     case S_P2M: return launch_p2m(h->dt, h->d_leaf, (int)P.leaf_nodes.size(), rho, h->d_mp, h->d_mp32, s);
     case S_M2M: return launch_m2m(h->dt, st.a, st.b, h->d_mp, h->d_mp32, s);
-    case S_M2L:
-      if (h->precision == OCTO_MIXED)
-        return launch_m2l_interior_f32(h->dt, h->d_interior, (int)P.interior_nodes.size(), h->st, h->d_mp32,
-                                       h->d_loc, s);
-      return launch_m2l_interior(h->dt, h->d_interior, (int)P.interior_nodes.size(), h->st, h->d_mp, h->d_loc, s);
-    case S_CONV:
-      if (h->precision == OCTO_MIXED)
-        return launch_leaf_conv_mixed(h->dt, h->d_leaf, (int)P.leaf_nodes.size(), h->st, h->d_mp, h->d_loc, s);
-      return launch_leaf_conv(h->dt, h->d_leaf, (int)P.leaf_nodes.size(), h->st, h->d_mp, h->d_loc, s);
-    case S_BOUNDARY:
-      return launch_m2l_boundary(h->dt, h->d_boundary, (int)P.boundary_nodes.size(), h->st, h->d_mp, h->d_loc, s);
-    case S_CROSS_FULL: return launch_cross(h->dt, h->xf, CrossList{nullptr, nullptr, nullptr, 0}, h->d_mp, h->d_loc, s);
-    case S_CROSS_LEAF: return launch_cross(h->dt, CrossList{nullptr, nullptr, nullptr, 0}, h->xl, h->d_mp, h->d_loc, s);
+    case S_M2L: return launch_interior_items(h->dt, interact_args(h), s);
+    case S_CONV: return launch_leaf_items(h->dt, interact_args(h), s);
+    case S_PERSIST: return launch_persistent(h->dt, interact_args(h), s);
+    case S_CROSS_FULL:
+      return launch_cross_list(h->dt, h->xf, true, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
+    case S_CROSS_LEAF:
+      return launch_cross_list(h->dt, h->xl, false, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
     case S_L2L: return launch_l2l(h->dt, st.a, st.b, h->d_mp, h->d_loc, phi, g, h->n_leaf_cells(), s);
   }
   return cudaErrorInvalidValue;
@@ -269,6 +332,55 @@ std::vector<Kappa> make_kappa(int R) {
         k[(size_t)(x + R) + W * (y + R) + (size_t)W * W * (z + R)] = v;
       }
   return k;
+}
+
+}  // namespace
+
+namespace {
+
+// Project autotuner of the batched interaction phase: after one upward pass with
+// this rho, times the interaction stages under each strategy (per-kind launches;
+// persistent queue with the 1- and 2-blocks-per-SM register budgets) on the
+// handle's own tree and keeps the fastest.  Runs once per handle, on the private
+// stream, ordered after the caller's pending work.
+int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
+  cudaStream_t ts = h->cap_stream;
+  cudaEvent_t ready = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) e = cudaEventRecord(ready, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ts, ready, 0);
+  const bool prof = h->profile;
+  h->profile = false;
+  if (e == cudaSuccess) e = enq_upward(h, rho, ts);
+  struct Cand {
+    int mode, minb;
+  } cands[3] = {{MODE_PER_KIND, 1}, {MODE_PERSISTENT, 1}, {MODE_PERSISTENT, 2}};
+  int best = 0;
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+    h->mode = cands[c].mode;
+    h->min_blocks = cands[c].minb;
+    e = rebuild_stages(h);
+    if (e == cudaSuccess) e = enq_interact(h, ts);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(t0, ts);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = enq_interact(h, ts);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, ts);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    h->tune_ms[c] = ms / 3.0f;
+    if (h->tune_ms[c] < h->tune_ms[best]) best = c;
+  }
+  h->profile = prof;
+  if (ready) cudaEventDestroy(ready);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+  h->mode = cands[best].mode;
+  h->min_blocks = cands[best].minb;
+  e = rebuild_stages(h);
+  return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "autotune");
 }
 
 }  // namespace
@@ -339,7 +451,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   }
   // split cross-level targets into interior (full expansion) and leaf targets
   {
-    std::vector<int64_t> ft, fs, fsrc, lt, ls, lsrc;
+    std::vector<int64_t> ft, fs, fm, fsrc, lt, ls, lm, lsrc;
     fs.push_back(0);
     ls.push_back(0);
     for (size_t i = 0; i < P.x_targets.size(); ++i) {
@@ -347,8 +459,11 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
       bool full = P.children[8 * (tg / kCells)] >= 0;
       auto& T = full ? ft : lt;
       auto& S = full ? fs : ls;
+      auto& M = full ? fm : lm;
       auto& SRC = full ? fsrc : lsrc;
       T.push_back(tg);
+      M.push_back((int64_t)SRC.size() + (P.x_mid[i] - P.x_start[i]));
+      (full ? h->xf_p2p : h->xl_p2p) += P.x_start[i + 1] - P.x_mid[i];
       for (int64_t k = P.x_start[i]; k < P.x_start[i + 1]; ++k) SRC.push_back(P.x_sources[k]);
       S.push_back((int64_t)SRC.size());
     }
@@ -358,11 +473,15 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     h->xl_pairs = (int64_t)lsrc.size();
     up(&h->d_xf_t, ft);
     up(&h->d_xf_s, fs);
+    up(&h->d_xf_m, fm);
     up(&h->d_xf_src, fsrc);
     up(&h->d_xl_t, lt);
     up(&h->d_xl_s, ls);
+    up(&h->d_xl_m, lm);
     up(&h->d_xl_src, lsrc);
   }
+  up(&h->d_st_slot, P.st_slot);
+  up(&h->d_st_slot_off, P.st_slot_off);
   const int64_t NC = (int64_t)P.n_nodes * kCells;
   if (e == cudaSuccess) e = cudaMalloc(&h->d_mp, sizeof(double) * N_MP * NC);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_loc, sizeof(double) * N_LOC * NC);
@@ -397,9 +516,9 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   for (int32_t v : P.st_near)
     for (int k = 0; k < 3; ++k) RN = std::max(RN, std::abs((int)(int8_t)((v >> (8 * k)) & 0xff)));
   h->st = Stencils{h->d_st_parity, P.n_st,       h->d_st_root,   (int)P.st_root.size(), h->d_st_near,
-                   (int)P.st_near.size(), h->d_kappa, h->d_kappa32, R, RN};
-  h->xf = CrossList{h->d_xf_t, h->d_xf_s, h->d_xf_src, h->n_xf};
-  h->xl = CrossList{h->d_xl_t, h->d_xl_s, h->d_xl_src, h->n_xl};
+                   (int)P.st_near.size(), h->d_kappa, h->d_kappa32, R, RN, h->d_st_slot, h->d_st_slot_off};
+  h->xf = CrossList{h->d_xf_t, h->d_xf_s, h->d_xf_src, h->n_xf, h->d_xf_m};
+  h->xl = CrossList{h->d_xl_t, h->d_xl_s, h->d_xl_src, h->n_xl, h->d_xl_m};
   e = configure_kernels();
   if (e == cudaSuccess) e = configure_kernels_mixed();
   if (e == cudaSuccess)
@@ -411,14 +530,47 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     delete h;
     return create_fail(OCTO_ECUDA, m);
   }
-  make_stages(h);
-  h->ev.resize(h->stages.size() + 1, nullptr);
-  for (auto& ev : h->ev)
-    if (cudaEventCreate(&ev) != cudaSuccess) {
+  // persistent work queue: interior items of the root, then of the other levels,
+  // then leaf items with refined neighbours, then the other leaf items
+  {
+    std::vector<int32_t> q;
+    auto push = [&](int node, int kind) {
+      q.push_back((node << 2) | (kind << 1) | 0);
+      q.push_back((node << 2) | (kind << 1) | 1);
+    };
+    for (int k : P.interior_nodes)
+      if (P.level[k] == 0) push(k, 0);
+    for (int k : P.interior_nodes)
+      if (P.level[k] != 0) push(k, 0);
+    std::vector<char> bnd(P.n_nodes, 0);
+    for (int k : P.boundary_nodes) bnd[k] = 1;
+    for (int k : P.leaf_nodes)
+      if (bnd[k]) push(k, 1);
+    for (int k : P.leaf_nodes)
+      if (!bnd[k]) push(k, 1);
+    h->n_items = (int)q.size();
+    e = upload(&h->d_queue, q);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = configure_interact_kernels();
+    for (int mb = 1; mb <= 2 && e == cudaSuccess; ++mb)
+      e = persistent_blocks_per_sm(precision == OCTO_MIXED, mb, h->st, &h->persist_per_sm[mb]);
+    if (e != cudaSuccess) {
+      std::string m = std::string("work queue setup failed: ") + cudaGetErrorString(e);
       free_all(h);
       delete h;
-      return create_fail(OCTO_ECUDA, "event creation failed");
+      return create_fail(OCTO_ECUDA, m);
     }
+  }
+  h->mode = MODE_PER_KIND;  // until the autotuner (or option 3) decides
+  e = rebuild_stages(h);
+  if (e != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return create_fail(OCTO_ECUDA, "event creation failed");
+  }
   *out = h;
   return OCTO_OK;
 }
@@ -446,6 +598,10 @@ int octo_fmm_downward(octo_fmm_t h, double* phi, double* g, void* stream) {
 int octo_fmm_forces(octo_fmm_t h, const double* rho, double* phi, double* g, void* stream) {
   if (!h || !rho || !phi || !g) return h ? fail(h, OCTO_EINVAL, "null buffer") : OCTO_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (h->requested_mode == MODE_AUTO && h->tune_ms[0] == 0.0f) {
+    int rc = autotune(h, rho, s);
+    if (rc != OCTO_OK) return rc;
+  }
   if (!h->use_graph) {
     cudaError_t e = enq_solve(h, rho, phi, g, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "forces");
@@ -506,13 +662,58 @@ int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host,
 int octo_fmm_backward(octo_fmm_t h, const double* dphi, const double* dg, double* drho, void* stream) {
   if (!h || !dphi || !dg || !drho) return h ? fail(h, OCTO_EINVAL, "null buffer") : OCTO_EINVAL;
   if (!h->forward_done) return fail(h, OCTO_ESTATE, "backward needs a forward solve on this handle");
-  (void)stream;
-  return fail(h, OCTO_EINVAL, "backward is not available in this build");
+  const Plan& P = h->plan;
+  const int64_t NC = (int64_t)P.n_nodes * kCells;
+  cudaError_t e = cudaSuccess;
+  if (!h->d_mpb) {  // adjoint workspace, allocated on first use
+    std::vector<int32_t> general(P.interior_nodes);
+    general.insert(general.end(), P.boundary_nodes.begin(), P.boundary_nodes.end());
+    h->n_general = (int)general.size();
+    e = upload(&h->d_general, general);
+    // the adjoint kernels keep large per-thread frames: make sure the stack limit covers them
+    size_t need = 0, cur = 0;
+    if (e == cudaSuccess) e = adjoint_local_bytes(&need);
+    if (e == cudaSuccess) e = cudaDeviceGetLimit(&cur, cudaLimitStackSize);
+    if (e == cudaSuccess && cur < need) e = cudaDeviceSetLimit(cudaLimitStackSize, need);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_mpb, sizeof(double) * N_MP * NC);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_locb, sizeof(double) * N_LOC * NC);
+    if (e != cudaSuccess) {
+      cudaFree(h->d_mpb);
+      cudaFree(h->d_locb);
+      h->d_mpb = h->d_locb = nullptr;
+      return e == cudaErrorMemoryAllocation ? fail(h, OCTO_ENOMEM, "adjoint workspace") : cuda_fail(h, e, "backward setup");
+    }
+  }
+  BackwardArgs ba;
+  ba.mp = h->d_mp;
+  ba.loc = h->d_loc;
+  ba.mpb = h->d_mpb;
+  ba.locb = h->d_locb;
+  ba.phib = dphi;
+  ba.gb = dg;
+  ba.rhob = drho;
+  ba.NL = h->n_leaf_cells();
+  ba.leaf_nodes = h->d_leaf;
+  ba.n_leaf_nodes = (int)P.leaf_nodes.size();
+  ba.general_nodes = h->d_general;
+  ba.n_general = h->n_general;
+  ba.level_start = P.level_start.data();
+  ba.max_level = P.max_level;
+  ba.st = h->st;
+  ba.xf = h->xf;
+  ba.xl = h->xl;
+  ba.err = h->d_err;
+  e = launch_backward(h->dt, ba, (cudaStream_t)stream);
+  return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "backward");
 }
 
 int octo_fmm_stats(octo_fmm_t h, int64_t counts[4]) {
   if (!h || !counts) return OCTO_EINVAL;
   for (int i = 0; i < 4; ++i) counts[i] = h->plan.counts[i];
+  int err = 0;
+  cudaError_t e = cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stats");
+  if (err) return fail(h, OCTO_ECUDA, "a device-side index check failed (bits " + std::to_string(err) + ")");
   return OCTO_OK;
 }
 
@@ -546,6 +747,17 @@ int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value) {
     return OCTO_OK;
   }
   if (key == 0 && value >= 0) return OCTO_OK;
+  if (key == 3 && value >= MODE_AUTO && value <= MODE_PERSISTENT) {
+    h->requested_mode = (int)value;
+    if (value != MODE_AUTO) h->mode = (int)value;
+    cudaError_t e = rebuild_stages(h);
+    return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "set strategy");
+  }
+  if (key == 4 && (value == 1 || value == 2)) {
+    h->min_blocks = (int)value;
+    cudaError_t e = rebuild_stages(h);
+    return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "set blocks");
+  }
   if (key == 2 && (value == 0 || value == 1)) {
     h->profile = value != 0;
     if (h->gexec) {  // re-capture with or without the timing events
@@ -583,6 +795,20 @@ int octo_fmm_stage_times(octo_fmm_t h, float* ms, int cap) {
 }
 
 int octo_fmm_launches_per_solve(octo_fmm_t h) { return h ? count_launches(h) : 0; }
+
+int octo_fmm_get_option(octo_fmm_t h, int key, int64_t* value) {
+  if (!h || !value) return OCTO_EINVAL;
+  switch (key) {
+    case 1: *value = h->use_graph ? 1 : 0; return OCTO_OK;
+    case 2: *value = h->profile ? 1 : 0; return OCTO_OK;
+    case 3: *value = h->mode; return OCTO_OK;
+    case 4: *value = h->min_blocks; return OCTO_OK;
+    case 10:
+    case 11:
+    case 12: *value = (int64_t)(1000.0f * h->tune_ms[key - 10]); return OCTO_OK;
+  }
+  return fail(h, OCTO_EINVAL, "unknown option");
+}
 
 const char* octo_fmm_last_error(octo_fmm_t h) {
   if (h) return h->err.c_str();

@@ -1,0 +1,310 @@
+// Work items of the same-level interaction phase, as device functions run by a
+// block of 256 threads (4 parity classes of one node: half = 0 -> cells with even
+// z, half = 1 -> odd z).  They are called both by the per-kind kernels and by the
+// persistent work-queue kernel (kernels_interact.cu).
+//
+//  interior item: all same-level M2L into the cells of a refined node (the
+//                 parity stencil, sources in the 26 neighbours), results stored;
+//  leaf item:     the leaf-leaf pairs of a leaf node as a convolution with the
+//                 tabulated point-mass kernel (far stencil + near offsets, mass
+//                 halo in shared memory), plus the M2L from refined same-level
+//                 neighbours (refinement boundary), results stored.
+#pragma once
+#include <type_traits>
+
+#include "kernels.h"
+
+namespace octo {
+namespace items {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void cell_of(int half, int tid, int& p, int& zh, int& a, int& b, int& c) {
+  const int w = tid >> 5, lane = tid & 31;
+  p = half * 4 + (w >> 1);
+  zh = w & 1;
+  const int q = (zh << 5) + lane;
+  a = 2 * (q & 3) + (p & 1);
+  b = 2 * ((q >> 2) & 3) + ((p >> 1) & 1);
+  c = 2 * (q >> 4) + (p >> 2);
+}
+
+__device__ __forceinline__ void unpack(int e, int& dx, int& dy, int& dz) {
+  dx = (int)(int8_t)(e & 0xff);
+  dy = (int)(int8_t)((e >> 8) & 0xff);
+  dz = (int)(int8_t)((e >> 16) & 0xff);
+}
+
+// ------------------------------------------------------------ interior, float64
+__device__ __forceinline__ void interior_f64(const DevTree& t, int node, int half, const Stencils& st,
+                                             const double* __restrict__ mp, double* __restrict__ loc) {
+  int p, zh, a, b, c;
+  cell_of(half, threadIdx.x, p, zh, a, b, c);
+  const int lvl = t.level[node];
+  const int64_t NC = t.NC;
+  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
+  const double XA0 = mp[(F_X + 0) * NC + tgt], XA1 = mp[(F_X + 1) * NC + tgt], XA2 = mp[(F_X + 2) * NC + tgt];
+  double Oh[10], tOh[3];
+  {
+    const double inv_m = 1.0 / mp[tgt];
+    for (int i = 0; i < 10; ++i) Oh[i] = mp[(F_O + i) * NC + tgt] * inv_m;
+    tOh[0] = Oh[0] + Oh[3] + Oh[5];
+    tOh[1] = Oh[1] + Oh[6] + Oh[8];
+    tOh[2] = Oh[2] + Oh[7] + Oh[9];
+  }
+  const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
+  const int ntab = lvl == 0 ? st.n_root : st.n_st;
+  const int* nb = t.nbr + 27 * node;
+  Acc<double> acc;
+  acc_zero(acc);
+  for (int s = 0; s < ntab; ++s) {
+    int dx, dy, dz;
+    unpack(__ldg(tab + s), dx, dy, dz);
+    const int sa = a + dx, sb = b + dy, sc = c + dz;
+    const int snode = __ldg(nb + ((sa >> 3) + 1) + 3 * ((sb >> 3) + 1) + 9 * ((sc >> 3) + 1));
+    if (snode < 0) continue;
+    const int64_t src = (int64_t)snode * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
+    const double R0 = XA0 - __ldg(mp + (F_X + 0) * NC + src);
+    const double R1 = XA1 - __ldg(mp + (F_X + 1) * NC + src);
+    const double R2 = XA2 - __ldg(mp + (F_X + 2) * NC + src);
+    const double m = __ldg(mp + src);
+    double Q[6], O[10];
+    for (int i = 0; i < 6; ++i) Q[i] = __ldg(mp + (F_Q + i) * NC + src);
+    for (int i = 0; i < 10; ++i) O[i] = __ldg(mp + (F_O + i) * NC + src);
+    const double rinv = rsqrt_f64(fma(R0, R0, fma(R1, R1, R2 * R2)));
+    m2l_pair<true, true>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, acc);
+  }
+  acc_finish(acc);
+  loc[G_L0 * NC + tgt] = acc.L0;
+  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = acc.L1[i];
+  for (int i = 0; i < 6; ++i) loc[(G_L2 + i) * NC + tgt] = acc.L2[i];
+  for (int i = 0; i < 10; ++i) loc[(G_L3 + i) * NC + tgt] = acc.L3[i];
+  for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] = acc.dg[i];
+}
+
+// ------------------------------------------------------------ interior, float32
+// Positions relative to node centres in cell widths: R = x_A - (x_B + 8 o) for a
+// source in neighbour slot o.
+__device__ __forceinline__ void interior_f32(const DevTree& t, int node, int half, const Stencils& st,
+                                             const float* __restrict__ mp32, double* __restrict__ loc) {
+  int p, zh, a, b, c;
+  cell_of(half, threadIdx.x, p, zh, a, b, c);
+  const int lvl = t.level[node];
+  const int64_t NC = t.NC;
+  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
+  const float xA0 = mp32[(F_X + 0) * NC + tgt], xA1 = mp32[(F_X + 1) * NC + tgt], xA2 = mp32[(F_X + 2) * NC + tgt];
+  float Oh[10], tOh[3];
+  {
+    const float inv_m = 1.0f / mp32[tgt];
+    for (int i = 0; i < 10; ++i) Oh[i] = mp32[(F_O + i) * NC + tgt] * inv_m;
+    tOh[0] = Oh[0] + Oh[3] + Oh[5];
+    tOh[1] = Oh[1] + Oh[6] + Oh[8];
+    tOh[2] = Oh[2] + Oh[7] + Oh[9];
+  }
+  const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
+  const int ntab = lvl == 0 ? st.n_root : st.n_st;
+  const int* nb = t.nbr + 27 * node;
+  Acc<KF> acc;
+  acc_zero(acc);
+  for (int s = 0; s < ntab; ++s) {
+    int dx, dy, dz;
+    unpack(__ldg(tab + s), dx, dy, dz);
+    const int sa = a + dx, sb = b + dy, sc = c + dz;
+    const int ox = sa >> 3, oy = sb >> 3, oz = sc >> 3;
+    const int snode = __ldg(nb + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
+    if (snode < 0) continue;
+    const int64_t src = (int64_t)snode * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
+    const float R0 = xA0 - (__ldg(mp32 + (F_X + 0) * NC + src) + 8.0f * (float)ox);
+    const float R1 = xA1 - (__ldg(mp32 + (F_X + 1) * NC + src) + 8.0f * (float)oy);
+    const float R2 = xA2 - (__ldg(mp32 + (F_X + 2) * NC + src) + 8.0f * (float)oz);
+    const float m = __ldg(mp32 + src);
+    float Q[6], O[10];
+    for (int i = 0; i < 6; ++i) Q[i] = __ldg(mp32 + (F_Q + i) * NC + src);
+    for (int i = 0; i < 10; ++i) O[i] = __ldg(mp32 + (F_O + i) * NC + src);
+    const float rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
+    m2l_pair<true, true>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, acc);
+  }
+  Acc<double> d;
+  d.L0 = acc.L0.value();
+  for (int i = 0; i < 3; ++i) d.L1[i] = acc.L1[i].value(), d.dg[i] = acc.dg[i].value(), d.V[i] = acc.V[i].value();
+  for (int i = 0; i < 6; ++i) d.L2[i] = acc.L2[i].value();
+  for (int i = 0; i < 10; ++i) d.L3[i] = acc.L3[i].value();
+  d.W = acc.W.value();
+  acc_finish(d);
+  const double ih = 1.0 / t.h[lvl], ih2 = ih * ih, ih3 = ih2 * ih, ih4 = ih2 * ih2;
+  loc[G_L0 * NC + tgt] = d.L0 * ih;
+  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = d.L1[i] * ih2;
+  for (int i = 0; i < 6; ++i) loc[(G_L2 + i) * NC + tgt] = d.L2[i] * ih3;
+  for (int i = 0; i < 10; ++i) loc[(G_L3 + i) * NC + tgt] = d.L3[i] * ih4;
+  for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] = d.dg[i] * ih2;
+}
+
+// ------------------------------------------------------------ leaf item
+// Shared memory: float64 halo of radius R (float64 path), or float32 halo of
+// radius R plus float64 halo of the near radius (mixed path).
+__host__ __device__ inline size_t leaf_smem_bytes(const Stencils& st, bool mixed) {
+  const size_t H = 8 + 2 * st.radius, HN = 8 + 2 * st.near_radius;
+  return mixed ? sizeof(double) * HN * HN * HN + sizeof(float) * H * H * H : sizeof(double) * H * H * H;
+}
+
+// M2L from refined same-level neighbours into a leaf cell (leaf target: L0, L1, dg).
+template <bool MIXED, typename A>
+__device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int p, int zh, int a, int b, int c,
+                                               const Stencils& st, const double* __restrict__ mp,
+                                               const float* __restrict__ mp32, A& acc) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  const int64_t NC = t.NC;
+  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
+  const int* nb = t.nbr + 27 * node;
+  T xA0, xA1, xA2;
+  if constexpr (MIXED) {
+    xA0 = mp32[(F_X + 0) * NC + tgt], xA1 = mp32[(F_X + 1) * NC + tgt], xA2 = mp32[(F_X + 2) * NC + tgt];
+  } else {
+    xA0 = mp[(F_X + 0) * NC + tgt], xA1 = mp[(F_X + 1) * NC + tgt], xA2 = mp[(F_X + 2) * NC + tgt];
+  }
+  const T zero10[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int o = 0; o < 27; ++o) {
+    const int sn = nb[o];
+    if (sn < 0 || t.children[8 * sn] < 0) continue;  // refined neighbours only
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+    const int li = (p * 2 + zh) * 27 + o;
+    const int e0 = st.slot_off[li], e1 = st.slot_off[li + 1];
+    for (int e = e0; e < e1; ++e) {
+      int dx, dy, dz;
+      unpack(__ldg(st.slot + e), dx, dy, dz);
+      const int sa = a + dx, sb = b + dy, sc = c + dz;
+      if ((sa >> 3) != ox || (sb >> 3) != oy || (sc >> 3) != oz) continue;
+      const int64_t src = (int64_t)sn * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
+      T R0, R1, R2, m, Q[6], O[10], rinv;
+      if constexpr (MIXED) {
+        R0 = xA0 - (__ldg(mp32 + (F_X + 0) * NC + src) + 8.0f * (float)ox);
+        R1 = xA1 - (__ldg(mp32 + (F_X + 1) * NC + src) + 8.0f * (float)oy);
+        R2 = xA2 - (__ldg(mp32 + (F_X + 2) * NC + src) + 8.0f * (float)oz);
+        m = __ldg(mp32 + src);
+        for (int i = 0; i < 6; ++i) Q[i] = __ldg(mp32 + (F_Q + i) * NC + src);
+        for (int i = 0; i < 10; ++i) O[i] = __ldg(mp32 + (F_O + i) * NC + src);
+        rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
+      } else {
+        R0 = xA0 - __ldg(mp + (F_X + 0) * NC + src);
+        R1 = xA1 - __ldg(mp + (F_X + 1) * NC + src);
+        R2 = xA2 - __ldg(mp + (F_X + 2) * NC + src);
+        m = __ldg(mp + src);
+        for (int i = 0; i < 6; ++i) Q[i] = __ldg(mp + (F_Q + i) * NC + src);
+        for (int i = 0; i < 10; ++i) O[i] = __ldg(mp + (F_O + i) * NC + src);
+        rinv = rsqrt_f64(fma(R0, R0, fma(R1, R1, R2 * R2)));
+      }
+      m2l_pair<false, false>(R0, R1, R2, m, Q, O, zero10, zero10, rinv, acc);
+    }
+  }
+}
+
+template <bool MIXED>
+__device__ __forceinline__ void leaf_item(const DevTree& t, int node, int half, const Stencils& st,
+                                          const double* __restrict__ mp, const float* __restrict__ mp32,
+                                          double* __restrict__ loc, unsigned char* smem) {
+  const int R = st.radius, H = 8 + 2 * R, H2 = H * H, W = 2 * R + 1;
+  const int RN = st.near_radius, HN = 8 + 2 * RN, HN2 = HN * HN;
+  const int* nb = t.nbr + 27 * node;
+  double* halo64 = reinterpret_cast<double*>(smem);
+  float* halo32 = reinterpret_cast<float*>(smem + sizeof(double) * HN2 * HN);
+  bool refined_nbr = false;
+  for (int o = 0; o < 27; ++o) {
+    const int sn = nb[o];
+    refined_nbr |= sn >= 0 && t.children[8 * sn] >= 0;
+  }
+  __syncthreads();  // the previous item may still read the halo
+  for (int i = threadIdx.x; i < H2 * H; i += blockDim.x) {
+    const int hx = i % H - R, hy = (i / H) % H - R, hz = i / H2 - R;
+    const int sn = nb[((hx >> 3) + 1) + 3 * ((hy >> 3) + 1) + 9 * ((hz >> 3) + 1)];
+    double m = 0.0;
+    if (sn >= 0 && t.children[8 * sn] < 0) m = mp[(int64_t)sn * 512 + (hx & 7) + 8 * (hy & 7) + 64 * (hz & 7)];
+    if (MIXED) {
+      halo32[i] = (float)m;
+      if (hx >= -RN && hx < 8 + RN && hy >= -RN && hy < 8 + RN && hz >= -RN && hz < 8 + RN)
+        halo64[(hx + RN) + HN * (hy + RN) + HN2 * (hz + RN)] = m;
+    } else {
+      reinterpret_cast<double*>(smem)[i] = m;
+    }
+  }
+  __syncthreads();
+  int p, zh, a, b, c;
+  cell_of(half, threadIdx.x, p, zh, a, b, c);
+  const int lvl = t.level[node];
+  const int kbase = R + W * R + W * W * R;
+  const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
+  const int ntab = lvl == 0 ? st.n_root : st.n_st;
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // float64 sums, unit cell width
+  if (MIXED) {
+    KF f0, f1, f2, f3;
+    f0 = 0.0f, f1 = 0.0f, f2 = 0.0f, f3 = 0.0f;
+    const int base = (a + R) + H * (b + R) + H2 * (c + R);
+    for (int s = 0; s < ntab; ++s) {
+      int dx, dy, dz;
+      unpack(__ldg(tab + s), dx, dy, dz);
+      const float m = halo32[base + dx + H * dy + H2 * dz];
+      const float4 k = __ldg(st.kappa32 + kbase + dx + W * dy + W * W * dz);
+      f0.add(m * k.x);
+      f1.add(m * k.y);
+      f2.add(m * k.z);
+      f3.add(m * k.w);
+    }
+    const int baseN = (a + RN) + HN * (b + RN) + HN2 * (c + RN);
+    for (int s = 0; s < st.n_near; ++s) {
+      int dx, dy, dz;
+      unpack(__ldg(st.near_ + s), dx, dy, dz);
+      const double m = halo64[baseN + dx + HN * dy + HN2 * dz];
+      const double2* kp = reinterpret_cast<const double2*>(st.kappa + kbase + dx + W * dy + W * W * dz);
+      const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
+      s0 = fma(m, ka.x, s0);
+      s1 = fma(m, ka.y, s1);
+      s2 = fma(m, kb.x, s2);
+      s3 = fma(m, kb.y, s3);
+    }
+    s0 += f0.value();
+    s1 += f1.value();
+    s2 += f2.value();
+    s3 += f3.value();
+  } else {
+    const double* halo = reinterpret_cast<const double*>(smem);
+    const int base = (a + R) + H * (b + R) + H2 * (c + R);
+    for (int pass = 0; pass < 2; ++pass) {
+      const int* tb = pass == 0 ? tab : st.near_;
+      const int nt = pass == 0 ? ntab : st.n_near;
+      for (int s = 0; s < nt; ++s) {
+        int dx, dy, dz;
+        unpack(__ldg(tb + s), dx, dy, dz);
+        const double m = halo[base + dx + H * dy + H2 * dz];
+        const double2* kp = reinterpret_cast<const double2*>(st.kappa + kbase + dx + W * dy + W * W * dz);
+        const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
+        s0 = fma(m, ka.x, s0);
+        s1 = fma(m, ka.y, s1);
+        s2 = fma(m, kb.x, s2);
+        s3 = fma(m, kb.y, s3);
+      }
+    }
+  }
+  const double ih = 1.0 / t.h[lvl], ih2 = ih * ih;
+  double L0 = s0 * ih, L1[3] = {s1 * ih2, s2 * ih2, s3 * ih2}, dg[3] = {0.0, 0.0, 0.0};
+  if (refined_nbr) {  // block-uniform
+    if constexpr (MIXED) {
+      Acc<KF> acc;
+      acc_zero(acc);
+      boundary_pairs<true>(t, node, p, zh, a, b, c, st, mp, mp32, acc);
+      L0 += acc.L0.value() * ih;
+      for (int i = 0; i < 3; ++i) L1[i] += acc.L1[i].value() * ih2, dg[i] = acc.dg[i].value() * ih2;
+    } else {
+      Acc<double> acc;
+      acc_zero(acc);
+      boundary_pairs<false>(t, node, p, zh, a, b, c, st, mp, mp32, acc);
+      L0 += acc.L0;
+      for (int i = 0; i < 3; ++i) L1[i] += acc.L1[i], dg[i] = acc.dg[i];
+    }
+  }
+  const int64_t NC = t.NC;
+  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
+  loc[G_L0 * NC + tgt] = L0;
+  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = L1[i], loc[(G_DG + i) * NC + tgt] = dg[i];
+}
+
+}  // namespace items
+}  // namespace octo

@@ -25,6 +25,8 @@ struct Stencils {
   const float4* kappa32; // the same table rounded to float32
   int radius;            // R: maximum |offset component|
   int near_radius;       // maximum |offset component| of the near offsets
+  const int* slot;       // parity offsets per (parity, warp z-half, neighbour slot), see Plan::st_slot
+  const int* slot_off;
 };
 
 struct CrossList {
@@ -32,7 +34,39 @@ struct CrossList {
   const int64_t* start;
   const int64_t* sources;
   int n_targets;
+  const int64_t* mid;    // per target: first near (P2P) partner; far (M2L) partners precede it
 };
+
+// Batched same-level interaction phase (kernels_interact.cu).
+struct InteractArgs {
+  const double* mp;
+  const float* mp32;   // mixed precision only
+  double* loc;
+  Stencils st;
+  bool mixed;
+  const int* interior; // refined nodes (all levels)
+  int n_interior;
+  const int* leaf;     // leaf nodes (all levels)
+  int n_leaf;
+  const int* queue;    // persistent queue: (node << 2) | (kind << 1) | half, largest items first
+  int n_items;
+  int* counter;        // work counter of the persistent launch (device scratch)
+  int grid;            // blocks of the persistent launch (SMs x resident blocks per SM)
+  int min_blocks;      // launch-bounds variant of the persistent kernel (1 or 2)
+};
+cudaError_t configure_interact_kernels();
+// Resident blocks per SM of the persistent kernel variant (also sets its shared
+// memory limit); call outside stream capture.
+cudaError_t persistent_blocks_per_sm(bool mixed, int min_blocks, const Stencils& st, int* per_sm);
+cudaError_t launch_interior_items(const DevTree& t, const InteractArgs& a, cudaStream_t s);
+cudaError_t launch_leaf_items(const DevTree& t, const InteractArgs& a, cudaStream_t s);
+cudaError_t launch_persistent(const DevTree& t, const InteractArgs& a, cudaStream_t s);
+
+// Refinement-boundary interactions (kernels_boundary.cu).
+cudaError_t launch_boundary(const DevTree& t, const int* nodes, int n, const Stencils& st, const double* mp,
+                            const float* mp32, double* loc, bool mixed, cudaStream_t s);
+cudaError_t launch_cross_list(const DevTree& t, const CrossList& xl, bool full, const double* mp, double* loc,
+                              bool mixed, cudaStream_t s);
 
 // Once per process and device, before the first launch (opts into large shared memory).
 cudaError_t configure_kernels();
@@ -51,6 +85,29 @@ cudaError_t launch_leaf_conv(const DevTree& t, const int* nodes, int n_nodes, co
                              double* loc, cudaStream_t s);
 cudaError_t launch_cross(const DevTree& t, const CrossList& full, const CrossList& leaf, const double* mp,
                          double* loc, cudaStream_t s);
+// Adjoint of the float64 solve (kernels_adjoint.cu).
+struct BackwardArgs {
+  const double* mp;   // forward multipoles
+  const double* loc;  // forward local expansions (final, interior cells)
+  double* mpb;        // [20][NC] multipole adjoints (workspace)
+  double* locb;       // [23][NC] local-expansion adjoints (workspace)
+  const double* phib;
+  const double* gb;
+  double* rhob;
+  int64_t NL;
+  const int* leaf_nodes;
+  int n_leaf_nodes;
+  const int* general_nodes;  // interior nodes and leaf nodes with a refined neighbour
+  int n_general;
+  const int* level_start;    // host array [max_level + 2]
+  int max_level;
+  Stencils st;
+  CrossList xf, xl;
+  int* err;                  // device word: bits of failed index checks (see kernels_adjoint.cu)
+};
+cudaError_t launch_backward(const DevTree& t, const BackwardArgs& ba, cudaStream_t s);
+cudaError_t adjoint_local_bytes(size_t* out);
+
 // Mixed precision (kernels_mixed.cu): far-field M2L in float32 with compensated sums.
 cudaError_t launch_m2l_interior_f32(const DevTree& t, const int* nodes, int n_nodes, const Stencils& st,
                                     const float* mp32, double* loc, cudaStream_t s);

@@ -1,0 +1,128 @@
+// The same-level interaction phase as batched launches.
+//
+//  * per-kind launches: one grid over all interior items of every level, one grid
+//    over all leaf items;
+//  * persistent queue: one grid of (SMs x blocks per SM) blocks that pull items of
+//    both kinds, of every level, from a single atomic counter (largest items first),
+//    so that float32-heavy interior items and float64-heavy leaf items share the
+//    SMs and the tail of one kind overlaps the other.  The counter is reset by a
+//    memset issued before every launch; no block ever waits for another.
+// The autotuner in capi.cu times both on the actual tree and keeps the faster.
+#include "items.cuh"
+
+namespace octo {
+
+namespace {
+
+template <bool MIXED>
+__global__ void __launch_bounds__(items::kThreads) k_interior_items(DevTree t, const int* __restrict__ nodes,
+                                                                     Stencils st, const double* __restrict__ mp,
+                                                                     const float* __restrict__ mp32,
+                                                                     double* __restrict__ loc) {
+  const int node = nodes[blockIdx.x >> 1];
+  if (MIXED)
+    items::interior_f32(t, node, blockIdx.x & 1, st, mp32, loc);
+  else
+    items::interior_f64(t, node, blockIdx.x & 1, st, mp, loc);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(items::kThreads) k_leaf_items(DevTree t, const int* __restrict__ nodes, Stencils st,
+                                                                 const double* __restrict__ mp,
+                                                                 const float* __restrict__ mp32,
+                                                                 double* __restrict__ loc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  items::leaf_item<MIXED>(t, nodes[blockIdx.x >> 1], blockIdx.x & 1, st, mp, mp32, loc, smem);
+}
+
+// item = (node << 2) | (kind << 1) | half, kind 0 = interior, 1 = leaf
+template <bool MIXED, int MINB>
+__global__ void __launch_bounds__(items::kThreads, MINB)
+    k_persistent(DevTree t, const int* __restrict__ queue, int n_items, int* __restrict__ counter, Stencils st,
+                 const double* __restrict__ mp, const float* __restrict__ mp32, double* __restrict__ loc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int next;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int k = next;
+    if (k >= n_items) return;
+    const int it = queue[k];
+    const int node = it >> 2, half = it & 1;
+    if ((it >> 1) & 1) {
+      items::leaf_item<MIXED>(t, node, half, st, mp, mp32, loc, smem);
+    } else {
+      if (MIXED)
+        items::interior_f32(t, node, half, st, mp32, loc);
+      else
+        items::interior_f64(t, node, half, st, mp, loc);
+    }
+  }
+}
+
+// Resident blocks per SM of a persistent variant (sets its shared-memory limit);
+// called once per handle, outside any stream capture.
+template <bool MIXED, int MINB>
+cudaError_t persistent_occupancy(const Stencils& st, int* per_sm) {
+  const size_t smem = items::leaf_smem_bytes(st, MIXED);
+  cudaError_t e = cudaFuncSetAttribute(k_persistent<MIXED, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_persistent<MIXED, MINB>, items::kThreads, smem);
+  if (e == cudaSuccess && *per_sm < 1) e = cudaErrorInvalidConfiguration;
+  return e;
+}
+
+template <bool MIXED, int MINB>
+cudaError_t persistent_launch(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
+  const size_t smem = items::leaf_smem_bytes(a.st, MIXED);
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_persistent<MIXED, MINB><<<a.grid, items::kThreads, smem, s>>>(t, a.queue, a.n_items, a.counter, a.st, a.mp,
+                                                                  a.mp32, a.loc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t configure_interact_kernels() {
+  cudaError_t e = cudaSuccess;
+  const int big = 200 * 1024;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leaf_items<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leaf_items<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  return e;
+}
+
+cudaError_t launch_interior_items(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
+  if (a.n_interior == 0) return cudaSuccess;
+  if (a.mixed)
+    k_interior_items<true><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp, a.mp32, a.loc);
+  else
+    k_interior_items<false><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp, a.mp32, a.loc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_items(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
+  if (a.n_leaf == 0) return cudaSuccess;
+  const size_t smem = items::leaf_smem_bytes(a.st, a.mixed);
+  if (a.mixed)
+    k_leaf_items<true><<<2 * a.n_leaf, items::kThreads, smem, s>>>(t, a.leaf, a.st, a.mp, a.mp32, a.loc);
+  else
+    k_leaf_items<false><<<2 * a.n_leaf, items::kThreads, smem, s>>>(t, a.leaf, a.st, a.mp, a.mp32, a.loc);
+  return cudaGetLastError();
+}
+
+cudaError_t persistent_blocks_per_sm(bool mixed, int min_blocks, const Stencils& st, int* per_sm) {
+  if (mixed) return min_blocks == 2 ? persistent_occupancy<true, 2>(st, per_sm) : persistent_occupancy<true, 1>(st, per_sm);
+  return min_blocks == 2 ? persistent_occupancy<false, 2>(st, per_sm) : persistent_occupancy<false, 1>(st, per_sm);
+}
+
+cudaError_t launch_persistent(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
+  if (a.n_items == 0) return cudaSuccess;
+  if (a.grid < 1) return cudaErrorInvalidConfiguration;
+  if (a.mixed) return a.min_blocks == 2 ? persistent_launch<true, 2>(t, a, s) : persistent_launch<true, 1>(t, a, s);
+  return a.min_blocks == 2 ? persistent_launch<false, 2>(t, a, s) : persistent_launch<false, 1>(t, a, s);
+}
+
+}  // namespace octo

@@ -239,6 +239,29 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
         else if (dx || dy || dz)
           P.st_near.push_back(pack_offset(dx, dy, dz));
       }
+  // slot lists: a warp holds the cells (2i+px, 2j+py, 2k+pz), i, j in [0,4),
+  // k in {2 zh, 2 zh + 1} of one parity class (see the kernels' thread mapping)
+  P.st_slot.clear();
+  P.st_slot_off.assign(1, 0);
+  for (int p = 0; p < 8; ++p)
+    for (int zh = 0; zh < 2; ++zh)
+      for (int o = 0; o < 27; ++o) {
+        for (int s = 0; s < P.n_st; ++s) {
+          int32_t e = P.st_parity[(size_t)p * P.n_st + s];
+          int d[3] = {(int8_t)(e & 0xff), (int8_t)((e >> 8) & 0xff), (int8_t)((e >> 16) & 0xff)};
+          bool hit = false;
+          for (int k = 2 * zh; k < 2 * zh + 2 && !hit; ++k)
+            for (int j = 0; j < 4 && !hit; ++j)
+              for (int i = 0; i < 4 && !hit; ++i) {
+                int loc[3] = {2 * i + (p & 1), 2 * j + ((p >> 1) & 1), 2 * k + (p >> 2)};
+                int so = (floor_div8(loc[0] + d[0]) + 1) + 3 * (floor_div8(loc[1] + d[1]) + 1) +
+                         9 * (floor_div8(loc[2] + d[2]) + 1);
+                hit = so == o;
+              }
+          if (hit) P.st_slot.push_back(e);
+        }
+        P.st_slot_off.push_back((int32_t)P.st_slot.size());
+      }
 
   // ---------------- work lists ----------------
   P.interior_nodes.clear();
@@ -319,6 +342,7 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
   // (recursively) until each piece is far (M2L) or a leaf cell (P2P).
   struct XPair {
     int64_t tgt, src;
+    int kind;  // 0 M2L, 1 P2P
   };
   std::vector<XPair> xp;
   int64_t c_xm2l = 0, c_xp2p = 0;
@@ -386,8 +410,8 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
             bool far = well_separated(theta, A.level, A.I, b.level, b.I);
             if (far || b_leaf) {
               int64_t gb = (int64_t)b.node * kCells + b.loc;
-              xp.push_back({gA, gb});
-              xp.push_back({gb, gA});
+              xp.push_back({gA, gb, far ? 0 : 1});
+              xp.push_back({gb, gA, far ? 0 : 1});
               if (far)
                 c_xm2l += 2;
               else
@@ -401,19 +425,26 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
     }
   }
   std::sort(xp.begin(), xp.end(), [](const XPair& a, const XPair& b) {
-    return a.tgt != b.tgt ? a.tgt < b.tgt : a.src < b.src;
+    if (a.tgt != b.tgt) return a.tgt < b.tgt;
+    if (a.kind != b.kind) return a.kind < b.kind;
+    return a.src < b.src;
   });
   P.x_targets.clear();
   P.x_start.clear();
+  P.x_mid.clear();
   P.x_sources.resize(xp.size());
   for (size_t i = 0; i < xp.size(); ++i) {
     if (i == 0 || xp[i].tgt != xp[i - 1].tgt) {
       P.x_targets.push_back(xp[i].tgt);
       P.x_start.push_back((int64_t)i);
+      P.x_mid.push_back(-1);
     }
+    if (xp[i].kind == 1 && P.x_mid.back() < 0) P.x_mid.back() = (int64_t)i;
     P.x_sources[i] = xp[i].src;
   }
   P.x_start.push_back((int64_t)xp.size());
+  for (size_t t = 0; t < P.x_targets.size(); ++t)
+    if (P.x_mid[t] < 0) P.x_mid[t] = P.x_start[t + 1];
 
   P.counts[0] = c_m2l;
   P.counts[1] = c_xm2l;

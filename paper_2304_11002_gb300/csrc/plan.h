@@ -42,6 +42,11 @@ struct Plan {
   int n_st = 0;
   std::vector<int32_t> st_root;
   std::vector<int32_t> st_near;
+  // Per (parity p, z-half zh of a warp, neighbour slot o): the parity-stencil
+  // offsets for which at least one cell of the warp lands in slot o; list
+  // (p * 2 + zh) * 27 + o spans st_slot[st_slot_off[i] .. st_slot_off[i+1]).
+  std::vector<int32_t> st_slot;
+  std::vector<int32_t> st_slot_off;
 
   // ---- work lists ----
   std::vector<int32_t> interior_nodes;   // refined device nodes (all levels)
@@ -50,6 +55,7 @@ struct Plan {
   // cross-level pairs, CSR by target cell (global cell index = dnode*512 + local)
   std::vector<int64_t> x_targets;        // distinct target cells
   std::vector<int64_t> x_start;          // [n_targets+1]
+  std::vector<int64_t> x_mid;            // [n_targets]: first P2P entry (M2L entries come first)
   std::vector<int64_t> x_sources;        // source cell per entry
 
   // ordered interaction counts: same-level M2L, cross-level M2L, same-level P2P, cross-level P2P

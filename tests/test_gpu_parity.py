@@ -163,3 +163,25 @@ def test_errors_are_reported():
     with pytest.raises(binding.OctoError) as e:
         binding.octo_fmm_backward(fmm.handle, d, torch.empty((3, 4096), dtype=torch.float64, device="cuda"), d)
     assert e.value.code == -7
+
+
+@pytest.mark.parametrize("precision", [binding.OCTO_FP64, binding.OCTO_MIXED])
+def test_interaction_strategies_bit_identical(precision):
+    """Per-kind launches and the persistent work queue (both register budgets) run
+    the same item functions: identical results, and the autotuner picks one of them."""
+    w = W.adaptive_binary(3, 0.08)
+    r = torch.from_numpy(w.rho.reshape(-1).copy()).cuda()
+    outs = []
+    for mode, minb in ((1, 1), (2, 1), (2, 2)):
+        fmm = binding.OctoFMM(w.tree, 0.5, precision)
+        binding.octo_fmm_set_option(fmm.handle, 3, mode)
+        binding.octo_fmm_set_option(fmm.handle, 4, minb)
+        phi, g = fmm.forces(r)
+        outs.append((phi.clone(), g.clone()))
+    for phi, g in outs[1:]:
+        assert torch.equal(phi, outs[0][0]) and torch.equal(g, outs[0][1])
+    fmm = binding.OctoFMM(w.tree, 0.5, precision)
+    phi, g = fmm.forces(r)
+    assert binding.octo_fmm_get_option(fmm.handle, 3) in (1, 2)
+    assert all(binding.octo_fmm_get_option(fmm.handle, k) > 0 for k in (10, 11, 12))
+    assert torch.equal(phi, outs[0][0]) and torch.equal(g, outs[0][1])
