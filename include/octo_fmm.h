@@ -158,15 +158,17 @@ int octo_fmm_launches_per_solve(octo_fmm_t h);
  * "l2l_l2").  octo_fmm_stage_count returns their number; octo_fmm_stage_info gives
  * stage i's name (owned by the handle), the interactions it processes (pairs), the
  * cells it writes, its algorithmic floating-point operations (the per-pair
- * expression as written, a fused multiply-add counting two) and its algorithmic
- * HBM bytes (tree passes: every value read or written once); any output pointer
- * may be NULL.  With option key 2 set to 1, the captured graph records a
+ * expression as written, a fused multiply-add counting two), how many of those
+ * run in float64, and its algorithmic HBM bytes (tree passes: every value read or
+ * written once); any output pointer may be NULL.  The stage list can change when
+ * the interaction strategy changes (option 3, autotuning on the first forces call).
+ * With option key 2 set to 1, the captured graph records a
  * CUDA event before every stage and after the last one; after the stream has
  * completed a forces call, octo_fmm_stage_times writes each stage's elapsed time in
  * milliseconds into ms[0..count) and returns count (cap must be >= count). */
 int octo_fmm_stage_count(octo_fmm_t h);
 int octo_fmm_stage_info(octo_fmm_t h, int i, const char** name, int64_t* pairs, int64_t* cells, int64_t* flops,
-                        int64_t* bytes);
+                        int64_t* flops64, int64_t* bytes);
 int octo_fmm_stage_times(octo_fmm_t h, float* ms, int cap);
 
 /* Message for the last failing call on h (or for create failures, h = NULL). */

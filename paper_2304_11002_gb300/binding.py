@@ -69,7 +69,8 @@ def lib() -> ctypes.CDLL:
         L.octo_fmm_launches_per_solve.argtypes = [vp]
         L.octo_fmm_stage_count.argtypes = [vp]
         i64p = ctypes.POINTER(ctypes.c_int64)
-        L.octo_fmm_stage_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i64p, i64p, i64p, i64p]
+        L.octo_fmm_stage_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i64p, i64p, i64p, i64p,
+                                          i64p]
         L.octo_fmm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
         L.octo_fmm_last_error.argtypes = [vp]
         L.octo_fmm_last_error.restype = ctypes.c_char_p
@@ -194,12 +195,12 @@ def octo_fmm_stage_count(h) -> int:
 
 
 def octo_fmm_stage_info(h, i: int) -> dict:
-    """name, pairs, cells, flops, bytes of stage i."""
+    """name, pairs, cells, flops, flops64 (the float64 part), bytes of stage i."""
     name = ctypes.c_char_p()
-    v = [ctypes.c_int64() for _ in range(4)]
+    v = [ctypes.c_int64() for _ in range(5)]
     _check(lib().octo_fmm_stage_info(h, int(i), ctypes.byref(name), *[ctypes.byref(x) for x in v]), h)
     return {"name": name.value.decode(), "pairs": int(v[0].value), "cells": int(v[1].value),
-            "flops": int(v[2].value), "bytes": int(v[3].value)}
+            "flops": int(v[2].value), "flops64": int(v[3].value), "bytes": int(v[4].value)}
 
 
 def octo_fmm_stage_times(h) -> np.ndarray:

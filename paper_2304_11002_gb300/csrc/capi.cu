@@ -58,7 +58,8 @@ struct octo_fmm {
   double *d_mpb = nullptr, *d_locb = nullptr;  // adjoint workspace
   int* d_general = nullptr;
   int n_general = 0;
-  int *d_st_slot = nullptr, *d_st_slot_off = nullptr;
+  int *d_cell_ent = nullptr, *d_cell_ent_off = nullptr, *d_bnd_index = nullptr;
+  unsigned short* d_bnd_perm = nullptr;
   int64_t xf_p2p = 0, xl_p2p = 0;  // near (P2P) entries of the cross-level lists
   int n_xf = 0, n_xl = 0;
   int64_t xf_pairs = 0, xl_pairs = 0;
@@ -84,6 +85,7 @@ struct octo_fmm {
     int64_t pairs;  // interactions processed (0 for tree passes)
     int64_t cells;  // cells processed
     int64_t flops;  // algorithmic floating-point operations
+    int64_t flops64;  // of which in float64
     int64_t bytes;  // algorithmic HBM bytes of the tree passes
   };
   std::vector<Stage> stages;
@@ -115,7 +117,8 @@ void free_all(octo_fmm* h) {
                   h->d_ijk,      h->d_interior, h->d_leaf,  h->d_boundary, h->d_st_parity, h->d_st_root,
                   h->d_st_near,  h->d_kappa,   h->d_xf_t,   h->d_xf_s,     h->d_xf_src,  h->d_xl_t,
                   h->d_xl_s,     h->d_xl_src,  h->d_mp,     h->d_loc,      h->d_io,        h->d_mp32,
-                  h->d_xf_m,     h->d_xl_m,    h->d_st_slot, h->d_st_slot_off, h->d_mpb, h->d_locb,
+                  h->d_xf_m,     h->d_xl_m,    h->d_cell_ent, h->d_cell_ent_off, h->d_bnd_perm,
+                  h->d_bnd_index, h->d_mpb,    h->d_locb,
                   h->d_general,  h->d_queue,   h->d_counter, h->d_err,
                   h->d_kappa32};
   for (void* p : ptrs)
@@ -178,23 +181,34 @@ void make_stages(octo_fmm* h) {
   const Plan& P = h->plan;
   auto add = [&](int kind, int a, int b, std::string name, int64_t pairs, int64_t cells) {
     // algorithmic flops and bytes of the stage (bytes: each value read or written once)
-    int64_t flops = 0, bytes = 0;
+    // Far-field flops run in float32 in mixed mode; near-field (P2P) flops are always float64.
+    int64_t far = 0, near = 0, bytes = 0;
+    const int64_t f_int = m2l_pair_flops<true, true>(), f_leaf = m2l_pair_flops<false, false>();
     switch (kind) {
       case S_P2M: bytes = cells * 16; break;                      // rho in, m out
       case S_M2M: bytes = cells * (8 * 20 + 20) * 8; break;        // 8 children in, parent out
-      case S_M2L: flops = pairs * m2l_pair_flops<true, true>(); break;
+      case S_M2L: far = pairs * f_int; break;
       case S_CONV:
-        flops = (pairs - P.kernel_pairs[3]) * kConvFlopsPerPair + P.kernel_pairs[3] * m2l_pair_flops<false, false>();
+        far = P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
+        near = P.kernel_pairs[2] * kConvFlopsPerPair;
         break;
       case S_PERSIST:
-        flops = P.kernel_pairs[0] * m2l_pair_flops<true, true>() + (P.kernel_pairs[1] + P.kernel_pairs[2]) * kConvFlopsPerPair +
-                P.kernel_pairs[3] * m2l_pair_flops<false, false>();
+        far = P.kernel_pairs[0] * f_int + P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
+        near = P.kernel_pairs[2] * kConvFlopsPerPair;
         break;
-      case S_CROSS_FULL: flops = (pairs - h->xf_p2p) * m2l_pair_flops<true, true>() + h->xf_p2p * kP2PFlopsPerPair; break;
-      case S_CROSS_LEAF: flops = (pairs - h->xl_p2p) * m2l_pair_flops<false, false>() + h->xl_p2p * kP2PFlopsPerPair; break;
+      case S_CROSS_FULL:
+        far = (pairs - h->xf_p2p) * f_int;
+        near = h->xf_p2p * kP2PFlopsPerPair;
+        break;
+      case S_CROSS_LEAF:
+        far = (pairs - h->xl_p2p) * f_leaf;
+        near = h->xl_p2p * kP2PFlopsPerPair;
+        break;
       case S_L2L: bytes = cells * 52 * 8; break;                   // own L/X in + L out + parent share
     }
-    h->stages.push_back({kind, a, b, std::move(name), pairs, cells, flops, bytes});
+    const int64_t flops = far + near;
+    const int64_t flops64 = h->precision == OCTO_MIXED ? near : flops;
+    h->stages.push_back({kind, a, b, std::move(name), pairs, cells, flops, flops64, bytes});
   };
   h->stages.clear();
   if (!P.leaf_nodes.empty()) add(S_P2M, 0, 0, "p2m", 0, (int64_t)P.leaf_nodes.size() * kCells);
@@ -480,8 +494,10 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     up(&h->d_xl_m, lm);
     up(&h->d_xl_src, lsrc);
   }
-  up(&h->d_st_slot, P.st_slot);
-  up(&h->d_st_slot_off, P.st_slot_off);
+  up(&h->d_cell_ent, P.cell_ent);
+  up(&h->d_cell_ent_off, P.cell_ent_off);
+  up(&h->d_bnd_perm, P.bnd_perm);
+  up(&h->d_bnd_index, P.bnd_index);
   const int64_t NC = (int64_t)P.n_nodes * kCells;
   if (e == cudaSuccess) e = cudaMalloc(&h->d_mp, sizeof(double) * N_MP * NC);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_loc, sizeof(double) * N_LOC * NC);
@@ -516,13 +532,11 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   for (int32_t v : P.st_near)
     for (int k = 0; k < 3; ++k) RN = std::max(RN, std::abs((int)(int8_t)((v >> (8 * k)) & 0xff)));
   h->st = Stencils{h->d_st_parity, P.n_st,       h->d_st_root,   (int)P.st_root.size(), h->d_st_near,
-                   (int)P.st_near.size(), h->d_kappa, h->d_kappa32, R, RN, h->d_st_slot, h->d_st_slot_off};
+                   (int)P.st_near.size(), h->d_kappa, h->d_kappa32, R, RN, h->d_cell_ent, h->d_cell_ent_off,
+                   h->d_bnd_perm, h->d_bnd_index};
   h->xf = CrossList{h->d_xf_t, h->d_xf_s, h->d_xf_src, h->n_xf, h->d_xf_m};
   h->xl = CrossList{h->d_xl_t, h->d_xl_s, h->d_xl_src, h->n_xl, h->d_xl_m};
-  e = configure_kernels();
-  if (e == cudaSuccess) e = configure_kernels_mixed();
-  if (e == cudaSuccess)
-    e = launch_init_leaf(t, h->d_leaf, (int)P.leaf_nodes.size(), h->d_mp, h->d_mp32, h->cap_stream);
+  e = launch_init_leaf(t, h->d_leaf, (int)P.leaf_nodes.size(), h->d_mp, h->d_mp32, h->cap_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap_stream);
   if (e != cudaSuccess) {
     std::string m = std::string("init failed: ") + cudaGetErrorString(e);
@@ -772,12 +786,13 @@ int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value) {
 int octo_fmm_stage_count(octo_fmm_t h) { return h ? (int)h->stages.size() : 0; }
 
 int octo_fmm_stage_info(octo_fmm_t h, int i, const char** name, int64_t* pairs, int64_t* cells, int64_t* flops,
-                        int64_t* bytes) {
+                        int64_t* flops64, int64_t* bytes) {
   if (!h || i < 0 || i >= (int)h->stages.size()) return OCTO_EINVAL;
   if (name) *name = h->stages[i].name.c_str();
   if (pairs) *pairs = h->stages[i].pairs;
   if (cells) *cells = h->stages[i].cells;
   if (flops) *flops = h->stages[i].flops;
+  if (flops64) *flops64 = h->stages[i].flops64;
   if (bytes) *bytes = h->stages[i].bytes;
   return OCTO_OK;
 }

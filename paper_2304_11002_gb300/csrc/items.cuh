@@ -142,19 +142,24 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
 // ------------------------------------------------------------ leaf item
 // Shared memory: float64 halo of radius R (float64 path), or float32 halo of
 // radius R plus float64 halo of the near radius (mixed path).
+// (at least 512 x 7 doubles: the boundary results are exchanged through it).
 __host__ __device__ inline size_t leaf_smem_bytes(const Stencils& st, bool mixed) {
   const size_t H = 8 + 2 * st.radius, HN = 8 + 2 * st.near_radius;
-  return mixed ? sizeof(double) * HN * HN * HN + sizeof(float) * H * H * H : sizeof(double) * H * H * H;
+  const size_t halo = mixed ? sizeof(double) * HN * HN * HN + sizeof(float) * H * H * H : sizeof(double) * H * H * H;
+  return halo > sizeof(double) * 512 * 7 ? halo : sizeof(double) * 512 * 7;
 }
 
-// M2L from refined same-level neighbours into a leaf cell (leaf target: L0, L1, dg).
+// M2L from refined same-level neighbours into leaf cell l of a leaf node (leaf
+// target: L0, L1, dg).  The per-cell entry lists hold only offsets whose source
+// lies in the neighbour slot, so every iteration of every lane is a valid pair.
 template <bool MIXED, typename A>
-__device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int p, int zh, int a, int b, int c,
-                                               const Stencils& st, const double* __restrict__ mp,
-                                               const float* __restrict__ mp32, A& acc) {
+__device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l, const Stencils& st,
+                                               const double* __restrict__ mp, const float* __restrict__ mp32,
+                                               A& acc) {
   using T = typename std::conditional<MIXED, float, double>::type;
   const int64_t NC = t.NC;
-  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
+  const int a = l & 7, b = (l >> 3) & 7, c = l >> 6;
+  const int64_t tgt = (int64_t)node * 512 + l;
   const int* nb = t.nbr + 27 * node;
   T xA0, xA1, xA2;
   if constexpr (MIXED) {
@@ -167,13 +172,11 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int p
     const int sn = nb[o];
     if (sn < 0 || t.children[8 * sn] < 0) continue;  // refined neighbours only
     const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-    const int li = (p * 2 + zh) * 27 + o;
-    const int e0 = st.slot_off[li], e1 = st.slot_off[li + 1];
+    const int e0 = __ldg(st.cell_ent_off + l * 27 + o), e1 = __ldg(st.cell_ent_off + l * 27 + o + 1);
     for (int e = e0; e < e1; ++e) {
       int dx, dy, dz;
-      unpack(__ldg(st.slot + e), dx, dy, dz);
+      unpack(__ldg(st.cell_ent + e), dx, dy, dz);
       const int sa = a + dx, sb = b + dy, sc = c + dz;
-      if ((sa >> 3) != ox || (sb >> 3) != oy || (sc >> 3) != oz) continue;
       const int64_t src = (int64_t)sn * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
       T R0, R1, R2, m, Q[6], O[10], rinv;
       if constexpr (MIXED) {
@@ -286,19 +289,31 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, int half, 
   const double ih = 1.0 / t.h[lvl], ih2 = ih * ih;
   double L0 = s0 * ih, L1[3] = {s1 * ih2, s2 * ih2, s3 * ih2}, dg[3] = {0.0, 0.0, 0.0};
   if (refined_nbr) {  // block-uniform
+    // Boundary pairs with the threads re-assigned to the cells of this half in
+    // decreasing order of load (balanced warps); the results go back to the owning
+    // threads through shared memory (the halo is no longer needed).
+    __syncthreads();
+    double* res = reinterpret_cast<double*>(smem);  // [512][7]
+    const int lb = st.bnd_perm[(int64_t)st.bnd_index[node] * 512 + half * 256 + threadIdx.x];
+    double v[7];
     if constexpr (MIXED) {
       Acc<KF> acc;
       acc_zero(acc);
-      boundary_pairs<true>(t, node, p, zh, a, b, c, st, mp, mp32, acc);
-      L0 += acc.L0.value() * ih;
-      for (int i = 0; i < 3; ++i) L1[i] += acc.L1[i].value() * ih2, dg[i] = acc.dg[i].value() * ih2;
+      boundary_pairs<true>(t, node, lb, st, mp, mp32, acc);
+      v[0] = acc.L0.value() * ih;
+      for (int i = 0; i < 3; ++i) v[1 + i] = acc.L1[i].value() * ih2, v[4 + i] = acc.dg[i].value() * ih2;
     } else {
       Acc<double> acc;
       acc_zero(acc);
-      boundary_pairs<false>(t, node, p, zh, a, b, c, st, mp, mp32, acc);
-      L0 += acc.L0;
-      for (int i = 0; i < 3; ++i) L1[i] += acc.L1[i], dg[i] = acc.dg[i];
+      boundary_pairs<false>(t, node, lb, st, mp, mp32, acc);
+      v[0] = acc.L0;
+      for (int i = 0; i < 3; ++i) v[1 + i] = acc.L1[i], v[4 + i] = acc.dg[i];
     }
+    for (int i = 0; i < 7; ++i) res[lb * 7 + i] = v[i];
+    __syncthreads();
+    const int l = a + 8 * b + 64 * c;
+    L0 += res[l * 7];
+    for (int i = 0; i < 3; ++i) L1[i] += res[l * 7 + 1 + i], dg[i] = res[l * 7 + 4 + i];
   }
   const int64_t NC = t.NC;
   const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;

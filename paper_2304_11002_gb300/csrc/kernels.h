@@ -25,8 +25,10 @@ struct Stencils {
   const float4* kappa32; // the same table rounded to float32
   int radius;            // R: maximum |offset component|
   int near_radius;       // maximum |offset component| of the near offsets
-  const int* slot;       // parity offsets per (parity, warp z-half, neighbour slot), see Plan::st_slot
-  const int* slot_off;
+  const int* cell_ent;   // parity offsets per (cell, neighbour slot), see Plan::cell_ent
+  const int* cell_ent_off;
+  const unsigned short* bnd_perm;  // per boundary leaf node: cells of each half by decreasing load
+  const int* bnd_index;            // per node: row of bnd_perm or -1
 };
 
 struct CrossList {
@@ -37,7 +39,17 @@ struct CrossList {
   const int64_t* mid;    // per target: first near (P2P) partner; far (M2L) partners precede it
 };
 
-// Batched same-level interaction phase (kernels_interact.cu).
+// ------------------------------------------------------------ tree passes (kernels_fp64.cu)
+// mp32 (may be null): float32 copy of the multipoles for the mixed-precision path.
+cudaError_t launch_init_leaf(const DevTree& t, const int* leaf_nodes, int n_leaf_nodes, double* mp, float* mp32,
+                             cudaStream_t s);
+cudaError_t launch_p2m(const DevTree& t, const int* leaf_nodes, int n_leaf_nodes, const double* rho, double* mp,
+                       float* mp32, cudaStream_t s);
+cudaError_t launch_m2m(const DevTree& t, int node_begin, int node_end, double* mp, float* mp32, cudaStream_t s);
+cudaError_t launch_l2l(const DevTree& t, int node_begin, int node_end, const double* mp, double* loc, double* phi,
+                       double* g, int64_t n_leaf_cells, cudaStream_t s);
+
+// ------------------------------------------------------------ same-level interactions (kernels_interact.cu)
 struct InteractArgs {
   const double* mp;
   const float* mp32;   // mixed precision only
@@ -54,6 +66,7 @@ struct InteractArgs {
   int grid;            // blocks of the persistent launch (SMs x resident blocks per SM)
   int min_blocks;      // launch-bounds variant of the persistent kernel (1 or 2)
 };
+// Once per process and device (opts the leaf-item kernels into large shared memory).
 cudaError_t configure_interact_kernels();
 // Resident blocks per SM of the persistent kernel variant (also sets its shared
 // memory limit); call outside stream capture.
@@ -62,30 +75,11 @@ cudaError_t launch_interior_items(const DevTree& t, const InteractArgs& a, cudaS
 cudaError_t launch_leaf_items(const DevTree& t, const InteractArgs& a, cudaStream_t s);
 cudaError_t launch_persistent(const DevTree& t, const InteractArgs& a, cudaStream_t s);
 
-// Refinement-boundary interactions (kernels_boundary.cu).
-cudaError_t launch_boundary(const DevTree& t, const int* nodes, int n, const Stencils& st, const double* mp,
-                            const float* mp32, double* loc, bool mixed, cudaStream_t s);
+// ------------------------------------------------------------ cross-level pairs (kernels_boundary.cu)
 cudaError_t launch_cross_list(const DevTree& t, const CrossList& xl, bool full, const double* mp, double* loc,
                               bool mixed, cudaStream_t s);
 
-// Once per process and device, before the first launch (opts into large shared memory).
-cudaError_t configure_kernels();
-
-// mp32 (may be null): float32 copy of the multipoles for the mixed-precision path.
-cudaError_t launch_init_leaf(const DevTree& t, const int* leaf_nodes, int n_leaf_nodes, double* mp, float* mp32,
-                             cudaStream_t s);
-cudaError_t launch_p2m(const DevTree& t, const int* leaf_nodes, int n_leaf_nodes, const double* rho, double* mp,
-                       float* mp32, cudaStream_t s);
-cudaError_t launch_m2m(const DevTree& t, int node_begin, int node_end, double* mp, float* mp32, cudaStream_t s);
-cudaError_t launch_m2l_interior(const DevTree& t, const int* nodes, int n_nodes, const Stencils& st,
-                                const double* mp, double* loc, cudaStream_t s);
-cudaError_t launch_m2l_boundary(const DevTree& t, const int* nodes, int n_nodes, const Stencils& st,
-                                const double* mp, double* loc, cudaStream_t s);
-cudaError_t launch_leaf_conv(const DevTree& t, const int* nodes, int n_nodes, const Stencils& st, const double* mp,
-                             double* loc, cudaStream_t s);
-cudaError_t launch_cross(const DevTree& t, const CrossList& full, const CrossList& leaf, const double* mp,
-                         double* loc, cudaStream_t s);
-// Adjoint of the float64 solve (kernels_adjoint.cu).
+// ------------------------------------------------------------ adjoint (kernels_adjoint.cu)
 struct BackwardArgs {
   const double* mp;   // forward multipoles
   const double* loc;  // forward local expansions (final, interior cells)
@@ -107,15 +101,5 @@ struct BackwardArgs {
 };
 cudaError_t launch_backward(const DevTree& t, const BackwardArgs& ba, cudaStream_t s);
 cudaError_t adjoint_local_bytes(size_t* out);
-
-// Mixed precision (kernels_mixed.cu): far-field M2L in float32 with compensated sums.
-cudaError_t launch_m2l_interior_f32(const DevTree& t, const int* nodes, int n_nodes, const Stencils& st,
-                                    const float* mp32, double* loc, cudaStream_t s);
-cudaError_t launch_leaf_conv_mixed(const DevTree& t, const int* nodes, int n_nodes, const Stencils& st,
-                                   const double* mp, double* loc, cudaStream_t s);
-cudaError_t configure_kernels_mixed();
-
-cudaError_t launch_l2l(const DevTree& t, int node_begin, int node_end, const double* mp, double* loc, double* phi,
-                       double* g, int64_t n_leaf_cells, cudaStream_t s);
 
 }  // namespace octo

@@ -1,99 +1,14 @@
-// Interactions at refinement boundaries.
-//
-//  * Same-level M2L from refined neighbour nodes into leaf nodes: a leaf target
-//    node walks only its refined neighbour slots, and for each slot only the
-//    stencil offsets that reach that slot from some cell of the warp (lists built
-//    on the host), so warps do not sweep the whole stencil for a few valid pairs.
-//  * Cross-level pairs (a leaf cell and a cell of a finer refined region): one warp
-//    per target cell, lanes striding over its partners, a fixed butterfly
-//    reduction at the end (deterministic).  M2L partners come first in each list,
-//    then P2P partners (exact point-mass interaction, always float64).
-// Mixed precision runs the M2L parts in float32 with compensated sums.
-#include <type_traits>
-
+// Cross-level pairs: a leaf cell and a cell of a finer refined region (both
+// directions are listed).  One warp per target cell, lanes striding over its
+// partners, a fixed butterfly reduction at the end (deterministic).  M2L partners
+// come first in each list, then P2P partners (exact point-mass interaction, always
+// float64).  Mixed precision runs the M2L part in float32 with compensated sums,
+// operands scaled to the target's cell width.
 #include "kernels.h"
 
 namespace octo {
 
 namespace {
-
-__device__ __forceinline__ void unpack_b(int e, int& dx, int& dy, int& dz) {
-  dx = (int)(int8_t)(e & 0xff);
-  dy = (int)(int8_t)((e >> 8) & 0xff);
-  dz = (int)(int8_t)((e >> 16) & 0xff);
-}
-
-template <bool MIXED>
-__global__ void __launch_bounds__(256) k_boundary(DevTree t, const int* __restrict__ nodes, Stencils st,
-                                                  const double* __restrict__ mp, const float* __restrict__ mp32,
-                                                  double* __restrict__ loc) {
-  const int node = nodes[blockIdx.x >> 1];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = (blockIdx.x & 1) * 4 + (w >> 1), zh = w & 1;
-  const int q = (zh << 5) + lane;
-  const int a = 2 * (q & 3) + (p & 1), b = 2 * ((q >> 2) & 3) + ((p >> 1) & 1), c = 2 * (q >> 4) + (p >> 2);
-  const int64_t NC = t.NC;
-  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
-  const int* nb = t.nbr + 27 * node;
-  using T = typename std::conditional<MIXED, float, double>::type;
-  using A = typename std::conditional<MIXED, Acc<KF>, Acc<double>>::type;
-  T xA0, xA1, xA2;
-  if (MIXED) {
-    xA0 = mp32[(F_X + 0) * NC + tgt], xA1 = mp32[(F_X + 1) * NC + tgt], xA2 = mp32[(F_X + 2) * NC + tgt];
-  } else {
-    xA0 = mp[(F_X + 0) * NC + tgt], xA1 = mp[(F_X + 1) * NC + tgt], xA2 = mp[(F_X + 2) * NC + tgt];
-  }
-  const T zero10[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  A acc;
-  acc_zero(acc);
-  for (int o = 0; o < 27; ++o) {
-    const int sn = nb[o];
-    if (sn < 0 || t.children[8 * sn] < 0) continue;  // only refined neighbours
-    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-    const int li = (p * 2 + zh) * 27 + o;
-    const int e0 = st.slot_off[li], e1 = st.slot_off[li + 1];
-    for (int e = e0; e < e1; ++e) {
-      int dx, dy, dz;
-      unpack_b(__ldg(st.slot + e), dx, dy, dz);
-      const int sa = a + dx, sb = b + dy, sc = c + dz;
-      if ((sa >> 3) != ox || (sb >> 3) != oy || (sc >> 3) != oz) continue;
-      const int64_t src = (int64_t)sn * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
-      T R0, R1, R2, m, Q[6], O[10];
-      if (MIXED) {
-        R0 = xA0 - (__ldg(mp32 + (F_X + 0) * NC + src) + 8.0f * (float)ox);
-        R1 = xA1 - (__ldg(mp32 + (F_X + 1) * NC + src) + 8.0f * (float)oy);
-        R2 = xA2 - (__ldg(mp32 + (F_X + 2) * NC + src) + 8.0f * (float)oz);
-        m = __ldg(mp32 + src);
-        for (int i = 0; i < 6; ++i) Q[i] = __ldg(mp32 + (F_Q + i) * NC + src);
-        for (int i = 0; i < 10; ++i) O[i] = __ldg(mp32 + (F_O + i) * NC + src);
-      } else {
-        R0 = xA0 - __ldg(mp + (F_X + 0) * NC + src);
-        R1 = xA1 - __ldg(mp + (F_X + 1) * NC + src);
-        R2 = xA2 - __ldg(mp + (F_X + 2) * NC + src);
-        m = __ldg(mp + src);
-        for (int i = 0; i < 6; ++i) Q[i] = __ldg(mp + (F_Q + i) * NC + src);
-        for (int i = 0; i < 10; ++i) O[i] = __ldg(mp + (F_O + i) * NC + src);
-      }
-      T rinv;
-      if (MIXED)
-        rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
-      else
-        rinv = rsqrt_f64(fma(R0, R0, fma(R1, R1, R2 * R2)));
-      m2l_pair<false, false>(R0, R1, R2, m, Q, O, zero10, zero10, rinv, acc);
-    }
-  }
-  double L0, L1[3], dg[3];
-  if constexpr (MIXED) {
-    const double ih = 1.0 / t.h[t.level[node]], ih2 = ih * ih;
-    L0 = acc.L0.value() * ih;
-    for (int i = 0; i < 3; ++i) L1[i] = acc.L1[i].value() * ih2, dg[i] = acc.dg[i].value() * ih2;
-  } else {
-    L0 = acc.L0;
-    for (int i = 0; i < 3; ++i) L1[i] = acc.L1[i], dg[i] = acc.dg[i];
-  }
-  loc[G_L0 * NC + tgt] += L0;
-  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] += L1[i], loc[(G_DG + i) * NC + tgt] += dg[i];
-}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -196,16 +111,6 @@ __global__ void __launch_bounds__(128) k_cross_w(DevTree t, CrossList xl, const 
 }
 
 }  // namespace
-
-cudaError_t launch_boundary(const DevTree& t, const int* nodes, int n, const Stencils& st, const double* mp,
-                            const float* mp32, double* loc, bool mixed, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  if (mixed)
-    k_boundary<true><<<2 * n, 256, 0, s>>>(t, nodes, st, mp, mp32, loc);
-  else
-    k_boundary<false><<<2 * n, 256, 0, s>>>(t, nodes, st, mp, mp32, loc);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_cross_list(const DevTree& t, const CrossList& xl, bool full, const double* mp, double* loc,
                               bool mixed, cudaStream_t s) {

@@ -1,31 +1,12 @@
-// Float64 kernels of the three solve phases (paper Section VII-C): bottom-up
-// (P2M, M2M), same-level interactions (M2L with the angular-momentum correction,
-// the leaf-level monopole convolution that also carries P2P, cross-level pairs)
-// and top-down (L2L with L2P fused at leaf nodes).
+// Tree passes of the solve (paper Section VII-C): bottom-up (P2M, M2M) and
+// top-down (L2L with L2P fused at leaf nodes), in float64 for both precision
+// modes.  The same-level interactions are in items.cuh / kernels_interact.cu and
+// kernels_boundary.cu.
 #include "kernels.h"
 
 namespace octo {
 
 namespace {
-
-// Cell (a, b, c) handled by thread `tid` of a block covering `ncls` parity classes
-// starting at class `cls0`: each warp holds 32 cells of one parity class
-// (p = px + 2 py + 4 pz, 64 cells per class per node), so stencil offsets are
-// warp-uniform.
-__device__ __forceinline__ void parity_cell(int cls0, int tid, int& p, int& a, int& b, int& c) {
-  const int w = tid >> 5, lane = tid & 31;
-  p = cls0 + (w >> 1);
-  const int q = ((w & 1) << 5) + lane;
-  a = 2 * (q & 3) + (p & 1);
-  b = 2 * ((q >> 2) & 3) + ((p >> 1) & 1);
-  c = 2 * (q >> 4) + (p >> 2);
-}
-
-__device__ __forceinline__ void unpack(int e, int& dx, int& dy, int& dz) {
-  dx = (int)(int8_t)(e & 0xff);
-  dy = (int)(int8_t)((e >> 8) & 0xff);
-  dz = (int)(int8_t)((e >> 16) & 0xff);
-}
 
 // ---------------------------------------------------------------- init / P2M
 __global__ void k_init_leaf(DevTree t, const int* __restrict__ nodes, double* __restrict__ mp,
@@ -141,171 +122,6 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int node_begin, double* 
   }
 }
 
-// ---------------------------------------------------------------- M2L (general)
-// Same-level M2L for every cell of a node over its parity stencil, sources from
-// the 26 neighbouring subgrids.  Block = 256 threads = 4 parity classes; two
-// blocks per node.
-//  LEAF_TARGET = false: interior target nodes, all sources, results stored (=).
-//  LEAF_TARGET = true : leaf target nodes, only sources in refined neighbour
-//                       nodes (leaf-leaf pairs are in the convolution), added (+=).
-template <bool LEAF_TARGET>
-__global__ void __launch_bounds__(256) k_m2l(DevTree t, const int* __restrict__ nodes, Stencils st,
-                                              const double* __restrict__ mp, double* __restrict__ loc) {
-  const int node = nodes[blockIdx.x >> 1];
-  int p, a, b, c;
-  parity_cell((blockIdx.x & 1) * 4, threadIdx.x, p, a, b, c);
-  const int lvl = t.level[node];
-  const int64_t NC = t.NC;
-  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
-  const double XA0 = mp[(F_X + 0) * NC + tgt], XA1 = mp[(F_X + 1) * NC + tgt], XA2 = mp[(F_X + 2) * NC + tgt];
-  double Oh[10], tOh[3];
-  if (!LEAF_TARGET) {
-    const double inv_m = 1.0 / mp[tgt];
-    for (int i = 0; i < 10; ++i) Oh[i] = mp[(F_O + i) * NC + tgt] * inv_m;
-    tOh[0] = Oh[0] + Oh[3] + Oh[5];
-    tOh[1] = Oh[1] + Oh[6] + Oh[8];
-    tOh[2] = Oh[2] + Oh[7] + Oh[9];
-  }
-  const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
-  const int ntab = lvl == 0 ? st.n_root : st.n_st;
-  const int* nb = t.nbr + 27 * node;
-  Acc<double> acc;
-  acc_zero(acc);
-  for (int s = 0; s < ntab; ++s) {
-    int dx, dy, dz;
-    unpack(__ldg(tab + s), dx, dy, dz);
-    const int sa = a + dx, sb = b + dy, sc = c + dz;
-    const int slot = ((sa >> 3) + 1) + 3 * ((sb >> 3) + 1) + 9 * ((sc >> 3) + 1);
-    const int snode = __ldg(nb + slot);
-    if (snode < 0) continue;
-    if (LEAF_TARGET && __ldg(t.children + 8 * snode) < 0) continue;
-    const int64_t src = (int64_t)snode * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
-    const double R0 = XA0 - __ldg(mp + (F_X + 0) * NC + src);
-    const double R1 = XA1 - __ldg(mp + (F_X + 1) * NC + src);
-    const double R2 = XA2 - __ldg(mp + (F_X + 2) * NC + src);
-    const double m = __ldg(mp + src);
-    double Q[6], O[10];
-    for (int i = 0; i < 6; ++i) Q[i] = __ldg(mp + (F_Q + i) * NC + src);
-    for (int i = 0; i < 10; ++i) O[i] = __ldg(mp + (F_O + i) * NC + src);
-    const double rinv = rsqrt_f64(fma(R0, R0, fma(R1, R1, R2 * R2)));
-    m2l_pair<!LEAF_TARGET, !LEAF_TARGET>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, acc);
-  }
-  if (!LEAF_TARGET) {
-    acc_finish(acc);
-    loc[G_L0 * NC + tgt] = acc.L0;
-    for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = acc.L1[i];
-    for (int i = 0; i < 6; ++i) loc[(G_L2 + i) * NC + tgt] = acc.L2[i];
-    for (int i = 0; i < 10; ++i) loc[(G_L3 + i) * NC + tgt] = acc.L3[i];
-    for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] = acc.dg[i];
-  } else {
-    loc[G_L0 * NC + tgt] += acc.L0;
-    for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] += acc.L1[i];
-    for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] += acc.dg[i];
-  }
-}
-
-// ---------------------------------------------------------------- leaf convolution
-// Between two leaf cells of one level both expansions are monopoles at cell
-// centres, so R = -d h for the stencil offset d and the M2L reduces to the exact
-// point-mass field, identical in form to P2P:  L0 += -m / r,  L1 += -m D1 = m R / r^3.
-// With kappa0(d) = -1/|d| and kappa1(d) = -d/|d|^3 (unit cell width):
-//   L0 = (1/h) sum m kappa0,  L1 = (1/h^2) sum m kappa1
-// over the far parity stencil (M2L) and the near offsets (P2P), with the masses of
-// same-level leaf cells staged in shared memory (halo of radius R).
-// Only L0, L1 (and dg = 0) of leaf cells are ever used; they are stored (=).
-__global__ void __launch_bounds__(512) k_leaf_conv(DevTree t, const int* __restrict__ nodes, Stencils st,
-                                                   const double* __restrict__ mp, double* __restrict__ loc) {
-  extern __shared__ double halo[];
-  const int node = nodes[blockIdx.x];
-  const int R = st.radius, H = 8 + 2 * R, H2 = H * H, W = 2 * R + 1;
-  const int* nb = t.nbr + 27 * node;
-  for (int i = threadIdx.x; i < H2 * H; i += blockDim.x) {
-    const int hx = i % H - R, hy = (i / H) % H - R, hz = i / H2 - R;
-    const int slot = ((hx >> 3) + 1) + 3 * ((hy >> 3) + 1) + 9 * ((hz >> 3) + 1);
-    const int sn = nb[slot];
-    double m = 0.0;
-    if (sn >= 0 && t.children[8 * sn] < 0) m = mp[(int64_t)sn * 512 + (hx & 7) + 8 * (hy & 7) + 64 * (hz & 7)];
-    halo[i] = m;
-  }
-  __syncthreads();
-  int p, a, b, c;
-  parity_cell(0, threadIdx.x, p, a, b, c);
-  const int lvl = t.level[node];
-  const int base = (a + R) + H * (b + R) + H2 * (c + R);
-  const int kbase = R + W * R + W * W * R;
-  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
-  const int ntab = lvl == 0 ? st.n_root : st.n_st;
-  for (int pass = 0; pass < 2; ++pass) {
-    const int* tb = pass == 0 ? tab : st.near_;
-    const int nt = pass == 0 ? ntab : st.n_near;
-    for (int s = 0; s < nt; ++s) {
-      int dx, dy, dz;
-      unpack(__ldg(tb + s), dx, dy, dz);
-      const double m = halo[base + dx + H * dy + H2 * dz];
-      const double2* kp = reinterpret_cast<const double2*>(st.kappa + kbase + dx + W * dy + W * W * dz);
-      const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
-      s0 = fma(m, ka.x, s0);
-      s1 = fma(m, ka.y, s1);
-      s2 = fma(m, kb.x, s2);
-      s3 = fma(m, kb.y, s3);
-    }
-  }
-  const double ih = 1.0 / t.h[lvl];
-  const int64_t NC = t.NC;
-  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
-  loc[G_L0 * NC + tgt] = s0 * ih;
-  loc[(G_L1 + 0) * NC + tgt] = s1 * (ih * ih);
-  loc[(G_L1 + 1) * NC + tgt] = s2 * (ih * ih);
-  loc[(G_L1 + 2) * NC + tgt] = s3 * (ih * ih);
-  loc[(G_DG + 0) * NC + tgt] = 0.0;
-  loc[(G_DG + 1) * NC + tgt] = 0.0;
-  loc[(G_DG + 2) * NC + tgt] = 0.0;
-}
-
-// ---------------------------------------------------------------- cross-level pairs
-// Explicit pairs between a leaf cell and cells of a finer refined region (both
-// directions), one thread per target cell, general M2L (a leaf-leaf P2P pair is
-// the same expression with zero higher moments).  Results added (+=).
-template <bool FULL>
-__global__ void __launch_bounds__(128) k_cross(DevTree t, CrossList xl, const double* __restrict__ mp,
-                                               double* __restrict__ loc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= xl.n_targets) return;
-  const int64_t NC = t.NC;
-  const int64_t tgt = xl.targets[i];
-  const double XA0 = mp[(F_X + 0) * NC + tgt], XA1 = mp[(F_X + 1) * NC + tgt], XA2 = mp[(F_X + 2) * NC + tgt];
-  double Oh[10], tOh[3];
-  if (FULL) {
-    const double inv_m = 1.0 / mp[tgt];
-    for (int k = 0; k < 10; ++k) Oh[k] = mp[(F_O + k) * NC + tgt] * inv_m;
-    tOh[0] = Oh[0] + Oh[3] + Oh[5];
-    tOh[1] = Oh[1] + Oh[6] + Oh[8];
-    tOh[2] = Oh[2] + Oh[7] + Oh[9];
-  }
-  Acc<double> acc;
-  acc_zero(acc);
-  for (int64_t e = xl.start[i]; e < xl.start[i + 1]; ++e) {
-    const int64_t src = xl.sources[e];
-    const double R0 = XA0 - mp[(F_X + 0) * NC + src];
-    const double R1 = XA1 - mp[(F_X + 1) * NC + src];
-    const double R2 = XA2 - mp[(F_X + 2) * NC + src];
-    double Q[6], O[10];
-    for (int k = 0; k < 6; ++k) Q[k] = mp[(F_Q + k) * NC + src];
-    for (int k = 0; k < 10; ++k) O[k] = mp[(F_O + k) * NC + src];
-    const double rinv = rsqrt_f64(fma(R0, R0, fma(R1, R1, R2 * R2)));
-    m2l_pair<FULL, FULL>(R0, R1, R2, mp[src], Q, O, Oh, tOh, rinv, acc);
-  }
-  loc[G_L0 * NC + tgt] += acc.L0;
-  for (int k = 0; k < 3; ++k) loc[(G_L1 + k) * NC + tgt] += acc.L1[k];
-  for (int k = 0; k < 3; ++k) loc[(G_DG + k) * NC + tgt] += acc.dg[k];
-  if (FULL) {
-    acc_finish(acc);
-    for (int k = 0; k < 6; ++k) loc[(G_L2 + k) * NC + tgt] += acc.L2[k];
-    for (int k = 0; k < 10; ++k) loc[(G_L3 + k) * NC + tgt] += acc.L3[k];
-  }
-}
-
 // ---------------------------------------------------------------- L2L + L2P
 // Child expansion += parent expansion shifted by delta = X_child - X_parent
 // (exact for the cubic Taylor polynomial), dg carried down unshifted.  At leaf
@@ -385,10 +201,6 @@ __global__ void __launch_bounds__(256) k_l2l(DevTree t, int node_begin, const do
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-cudaError_t configure_kernels() {
-  return cudaFuncSetAttribute(k_leaf_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-}
-
 cudaError_t launch_init_leaf(const DevTree& t, const int* leaf_nodes, int n, double* mp, float* mp32,
                              cudaStream_t s) {
   if (n == 0) return cudaSuccess;
@@ -407,43 +219,6 @@ cudaError_t launch_m2m(const DevTree& t, int b, int e, double* mp, float* mp32, 
   if (e <= b) return cudaSuccess;
   k_m2m<<<2 * (e - b), 256, 0, s>>>(t, b, mp, mp32);
   return cudaGetLastError();
-}
-
-cudaError_t launch_m2l_interior(const DevTree& t, const int* nodes, int n, const Stencils& st, const double* mp,
-                                double* loc, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  k_m2l<false><<<2 * n, 256, 0, s>>>(t, nodes, st, mp, loc);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_m2l_boundary(const DevTree& t, const int* nodes, int n, const Stencils& st, const double* mp,
-                                double* loc, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  k_m2l<true><<<2 * n, 256, 0, s>>>(t, nodes, st, mp, loc);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_leaf_conv(const DevTree& t, const int* nodes, int n, const Stencils& st, const double* mp,
-                             double* loc, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  const int H = 8 + 2 * st.radius;
-  const size_t smem = sizeof(double) * H * H * H;
-  k_leaf_conv<<<n, 512, smem, s>>>(t, nodes, st, mp, loc);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cross(const DevTree& t, const CrossList& full, const CrossList& leaf, const double* mp,
-                         double* loc, cudaStream_t s) {
-  if (full.n_targets > 0) {
-    k_cross<true><<<(full.n_targets + 127) / 128, 128, 0, s>>>(t, full, mp, loc);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (leaf.n_targets > 0) {
-    k_cross<false><<<(leaf.n_targets + 127) / 128, 128, 0, s>>>(t, leaf, mp, loc);
-    return cudaGetLastError();
-  }
-  return cudaSuccess;
 }
 
 cudaError_t launch_l2l(const DevTree& t, int b, int e, const double* mp, double* loc, double* phi, double* g,

@@ -239,29 +239,25 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
         else if (dx || dy || dz)
           P.st_near.push_back(pack_offset(dx, dy, dz));
       }
-  // slot lists: a warp holds the cells (2i+px, 2j+py, 2k+pz), i, j in [0,4),
-  // k in {2 zh, 2 zh + 1} of one parity class (see the kernels' thread mapping)
-  P.st_slot.clear();
-  P.st_slot_off.assign(1, 0);
-  for (int p = 0; p < 8; ++p)
-    for (int zh = 0; zh < 2; ++zh)
-      for (int o = 0; o < 27; ++o) {
-        for (int s = 0; s < P.n_st; ++s) {
-          int32_t e = P.st_parity[(size_t)p * P.n_st + s];
-          int d[3] = {(int8_t)(e & 0xff), (int8_t)((e >> 8) & 0xff), (int8_t)((e >> 16) & 0xff)};
-          bool hit = false;
-          for (int k = 2 * zh; k < 2 * zh + 2 && !hit; ++k)
-            for (int j = 0; j < 4 && !hit; ++j)
-              for (int i = 0; i < 4 && !hit; ++i) {
-                int loc[3] = {2 * i + (p & 1), 2 * j + ((p >> 1) & 1), 2 * k + (p >> 2)};
-                int so = (floor_div8(loc[0] + d[0]) + 1) + 3 * (floor_div8(loc[1] + d[1]) + 1) +
-                         9 * (floor_div8(loc[2] + d[2]) + 1);
-                hit = so == o;
-              }
-          if (hit) P.st_slot.push_back(e);
-        }
-        P.st_slot_off.push_back((int32_t)P.st_slot.size());
+  // per-cell entry lists by neighbour slot
+  P.cell_ent.clear();
+  P.cell_ent_off.assign(1, 0);
+  std::vector<int32_t> cell_cnt(kCells * 27, 0);
+  for (int l = 0; l < kCells; ++l) {
+    const int loc[3] = {l & 7, (l >> 3) & 7, l >> 6};
+    const int p = (loc[0] & 1) + 2 * (loc[1] & 1) + 4 * (loc[2] & 1);
+    for (int o = 0; o < 27; ++o) {
+      for (int s = 0; s < P.n_st; ++s) {
+        int32_t e = P.st_parity[(size_t)p * P.n_st + s];
+        int d[3] = {(int8_t)(e & 0xff), (int8_t)((e >> 8) & 0xff), (int8_t)((e >> 16) & 0xff)};
+        int so = (floor_div8(loc[0] + d[0]) + 1) + 3 * (floor_div8(loc[1] + d[1]) + 1) +
+                 9 * (floor_div8(loc[2] + d[2]) + 1);
+        if (so == o) P.cell_ent.push_back(e);
       }
+      P.cell_ent_off.push_back((int32_t)P.cell_ent.size());
+      cell_cnt[l * 27 + o] = P.cell_ent_off.back() - P.cell_ent_off[P.cell_ent_off.size() - 2];
+    }
+  }
 
   // ---------------- work lists ----------------
   P.interior_nodes.clear();
@@ -278,6 +274,25 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
         if (m >= 0 && P.children[8 * m] >= 0) b = true;
       }
       if (b) P.boundary_nodes.push_back(k);
+    }
+  }
+  P.bnd_index.assign(n, -1);
+  P.bnd_perm.assign(P.boundary_nodes.size() * kCells, 0);
+  for (size_t bi = 0; bi < P.boundary_nodes.size(); ++bi) {
+    const int k = P.boundary_nodes[bi];
+    P.bnd_index[k] = (int32_t)bi;
+    std::vector<int> load(kCells, 0);
+    for (int l = 0; l < kCells; ++l)
+      for (int o = 0; o < 27; ++o) {
+        const int m = P.nbr[27 * k + o];
+        if (m >= 0 && P.children[8 * m] >= 0) load[l] += cell_cnt[l * 27 + o];
+      }
+    for (int half = 0; half < 2; ++half) {
+      std::vector<int> cells;
+      for (int l = 0; l < kCells; ++l)
+        if ((l >> 6 & 1) == half) cells.push_back(l);
+      std::stable_sort(cells.begin(), cells.end(), [&](int x, int y) { return load[x] > load[y]; });
+      for (int i = 0; i < 256; ++i) P.bnd_perm[bi * kCells + half * 256 + i] = (uint16_t)cells[i];
     }
   }
 

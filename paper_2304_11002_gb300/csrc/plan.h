@@ -42,11 +42,16 @@ struct Plan {
   int n_st = 0;
   std::vector<int32_t> st_root;
   std::vector<int32_t> st_near;
-  // Per (parity p, z-half zh of a warp, neighbour slot o): the parity-stencil
-  // offsets for which at least one cell of the warp lands in slot o; list
-  // (p * 2 + zh) * 27 + o spans st_slot[st_slot_off[i] .. st_slot_off[i+1]).
-  std::vector<int32_t> st_slot;
-  std::vector<int32_t> st_slot_off;
+  // Per (target cell local index l, neighbour slot o): the parity-stencil offsets
+  // of cell l whose source lands in slot o; list l * 27 + o spans
+  // cell_ent[cell_ent_off[i] .. cell_ent_off[i+1]).
+  std::vector<int32_t> cell_ent;
+  std::vector<int32_t> cell_ent_off;
+  // Leaf nodes with refined same-level neighbours: per node, the 256 cells of each
+  // half (even / odd z) ordered by decreasing number of pairs with those
+  // neighbours, so that the lanes of a warp get similar trip counts.
+  std::vector<uint16_t> bnd_perm;   // [n_boundary][2][256] local cell indices
+  std::vector<int32_t> bnd_index;   // per device node: row of bnd_perm, or -1
 
   // ---- work lists ----
   std::vector<int32_t> interior_nodes;   // refined device nodes (all levels)
