@@ -21,35 +21,36 @@ constexpr int kNComp = 56;
 
 __host__ __device__ constexpr int rank_off(int n) { return n * (n + 1) * (n + 2) / 6; }
 
+// The helpers below are loop-free so that they fold to constants immediately
+// inside the unrolled loops of the kernels (compile time stays short).
 __host__ __device__ constexpr int rank_of(int q) {
-  int n = 0;
-  while (rank_off(n + 1) <= q) ++n;
-  return n;
+  return q < 1 ? 0 : q < 4 ? 1 : q < 10 ? 2 : q < 20 ? 3 : q < 35 ? 4 : 5;
 }
 
+// position of the component with exponents (a, b, c): ranks before it, then
+// (n - a)(n - a + 1) / 2 components with a larger x exponent, then decreasing b
 __host__ __device__ constexpr int comp_index(int a, int b, int c) {
-  const int n = a + b + c;
-  int idx = 0;
-  for (int a2 = n; a2 > a; --a2) idx += n - a2 + 1;
-  return rank_off(n) + idx + (n - a - b);
+  return rank_off(a + b + c) + (b + c) * (b + c + 1) / 2 + c;
+}
+
+// m with m (m + 1) / 2 <= k < (m + 1)(m + 2) / 2, for k < 21
+__host__ __device__ constexpr int tri_root(int k) {
+  return k < 1 ? 0 : k < 3 ? 1 : k < 6 ? 2 : k < 10 ? 3 : k < 15 ? 4 : 5;
 }
 
 // exponent of axis d of component q
 __host__ __device__ constexpr int ex(int q, int d) {
-  const int n = rank_of(q);
-  int k = q - rank_off(n);
-  for (int a = n; a >= 0; --a) {
-    const int cnt = n - a + 1;
-    if (k < cnt) {
-      const int b = n - a - k;
-      return d == 0 ? a : (d == 1 ? b : n - a - b);
-    }
-    k -= cnt;
-  }
-  return -1;
+  return d == 0 ? rank_of(q) - tri_root(q - rank_off(rank_of(q)))
+         : d == 1 ? tri_root(q - rank_off(rank_of(q))) -
+                        (q - rank_off(rank_of(q)) - tri_root(q - rank_off(rank_of(q))) *
+                                                        (tri_root(q - rank_off(rank_of(q))) + 1) / 2)
+                  : q - rank_off(rank_of(q)) -
+                        tri_root(q - rank_off(rank_of(q))) * (tri_root(q - rank_off(rank_of(q))) + 1) / 2;
 }
 
-__host__ __device__ constexpr double fact(int n) { return n <= 1 ? 1.0 : n * fact(n - 1); }
+__host__ __device__ constexpr double fact(int n) {
+  return n <= 1 ? 1.0 : n == 2 ? 2.0 : n == 3 ? 6.0 : n == 4 ? 24.0 : n == 5 ? 120.0 : 720.0;
+}
 
 // copies of the component in the full tensor: n! / (a! b! c!)
 __host__ __device__ constexpr double mult(int q) {
