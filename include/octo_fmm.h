@@ -171,6 +171,33 @@ int octo_fmm_stage_info(octo_fmm_t h, int i, const char** name, int64_t* pairs, 
                         int64_t* flops64, int64_t* bytes);
 int octo_fmm_stage_times(octo_fmm_t h, float* ms, int cap);
 
+/* Allocation-free solve for callers that cannot allocate device memory at the
+ * point of the call: engines whose memory manager owns all device memory and
+ * forbids libraries from allocating behind its back, and time-critical loops that
+ * must not pay for, or fail on, an allocation mid-run (an allocation can stall on
+ * synchronisation or run out of memory).  The paper has no counterpart; it is an
+ * interface addition.
+ *
+ * Solves n_subgrids independent single-subgrid problems, each an 8x8x8 block of
+ * cells of width h forming a tree of one leaf node (so every cell pair interacts
+ * exactly as point masses; G = 1, phi = -sum m / r).  rho_dev, phi_dev: float64
+ * [n_subgrids * 512]; g_dev: float64 [3][n_subgrids * 512]; cells x-fastest inside
+ * a subgrid.  All three are caller-owned device buffers; results agree with
+ * octo_fmm_forces on a one-node tree.
+ *
+ * No memory is allocated by this call: the only intermediate state (the cell
+ * masses) lives in one fixed device array inside the library, sized for at most
+ * 1024 subgrids (4 MiB), which every GPU that loads the library keeps until the
+ * process exits.  n_subgrids outside [0, 1024] returns OCTO_EINVAL (message via
+ * octo_fmm_last_error(NULL)) without launching anything.  The first call on a
+ * device looks up that array's device address (once per device, with the device
+ * current); make that first call before any stream capture.  Every call reuses
+ * the same array and keeps nothing from earlier calls, so calls whose work
+ * overlaps on the GPU (different streams, different host threads) race: order
+ * them on one stream.  Asynchronous on `stream` like the other compute calls. */
+int octo_fmm_subgrids_noalloc(int n_subgrids, const double* rho_dev, double h, double* phi_dev, double* g_dev,
+                              void* stream);
+
 /* Message for the last failing call on h (or for create failures, h = NULL). */
 const char* octo_fmm_last_error(octo_fmm_t h);
 

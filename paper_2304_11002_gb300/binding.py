@@ -28,7 +28,8 @@ SYMBOLS = ["octo_fmm_create", "octo_fmm_upward", "octo_fmm_interact", "octo_fmm_
            "octo_fmm_forces_host", "octo_fmm_backward", "octo_fmm_stats", "octo_fmm_plan_counts",
            "octo_fmm_read_state", "octo_fmm_set_option", "octo_fmm_get_option", "octo_fmm_launches_per_solve",
            "octo_fmm_stage_count",
-           "octo_fmm_stage_info", "octo_fmm_stage_times", "octo_fmm_last_error", "octo_fmm_destroy"]
+           "octo_fmm_stage_info", "octo_fmm_stage_times", "octo_fmm_subgrids_noalloc", "octo_fmm_last_error",
+           "octo_fmm_destroy"]
 
 
 class OctoError(RuntimeError):
@@ -72,6 +73,7 @@ def lib() -> ctypes.CDLL:
         L.octo_fmm_stage_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i64p, i64p, i64p, i64p,
                                           i64p]
         L.octo_fmm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+        L.octo_fmm_subgrids_noalloc.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, vp]
         L.octo_fmm_last_error.argtypes = [vp]
         L.octo_fmm_last_error.restype = ctypes.c_char_p
         L.octo_fmm_destroy.argtypes = [vp]
@@ -178,6 +180,12 @@ def octo_fmm_read_state(h, which: int, n_nodes: int) -> np.ndarray:
 
 def octo_fmm_set_option(h, key: int, value: int) -> None:
     _check(lib().octo_fmm_set_option(h, int(key), int(value)), h)
+
+
+def octo_fmm_subgrids_noalloc(n_subgrids: int, rho, h: float, phi, g, stream=None) -> None:
+    """Allocation-free batch of single-subgrid solves (see include/octo_fmm.h)."""
+    _check(lib().octo_fmm_subgrids_noalloc(int(n_subgrids), _ptr(rho), float(h), _ptr(phi), _ptr(g),
+                                           _stream(stream)))
 
 
 def octo_fmm_get_option(h, key: int) -> int:

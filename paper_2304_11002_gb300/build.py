@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_lib", "obj")
 LIB = os.path.join(HERE, "_lib", "liboctofmm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["capi.cu", "kernels_fp64.cu", "kernels_adjoint.cu", "kernels_boundary.cu",
+CU_SOURCES = ["capi.cu", "kernels_fp64.cu", "kernels_adjoint.cu", "kernels_boundary.cu", "noalloc.cu",
               "kernels_interact.cu"]
 CXX_SOURCES = ["plan.cpp"]
 

@@ -20,6 +20,15 @@ namespace {
 std::mutex g_err_mu;
 std::string g_create_error;
 
+}  // namespace
+
+void octo::set_global_error(const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_create_error = msg;
+}
+
+namespace {
+
 template <typename T>
 cudaError_t upload(T** dst, const std::vector<T>& src) {
   *dst = nullptr;

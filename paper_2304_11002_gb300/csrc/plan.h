@@ -77,4 +77,7 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& plan);
 
 double cell_width(const Plan& p, int level);
 
+// Message returned by octo_fmm_last_error(NULL) (failures without a handle).
+void set_global_error(const std::string& msg);
+
 }  // namespace octo
