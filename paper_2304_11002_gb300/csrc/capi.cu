@@ -2,6 +2,7 @@
 // ordering on a stream and the CUDA-graph replay of the whole solve.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -38,6 +39,46 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
   return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
 }
 
+// Cross-level pair lists on the device, split by target: refined target cells
+// (full local expansion) and leaf target cells.  CSR per target, far partners
+// before near ones.
+struct CrossSet {
+  int64_t *d_ft = nullptr, *d_fs = nullptr, *d_fm = nullptr, *d_fsrc = nullptr;
+  int64_t *d_lt = nullptr, *d_ls = nullptr, *d_lm = nullptr, *d_lsrc = nullptr;
+  int n_f = 0, n_l = 0;
+  int64_t f_pairs = 0, l_pairs = 0, f_p2p = 0, l_p2p = 0;  // entries, of which near
+  CrossList f{}, l{};
+};
+
+cudaError_t upload_cross(const Plan& P, const std::vector<int64_t>& targets, const std::vector<int64_t>& start,
+                         const std::vector<int64_t>& mid, const std::vector<int64_t>& sources, CrossSet& cs) {
+  std::vector<int64_t> ft, fs(1, 0), fm, fsrc, lt, ls(1, 0), lm, lsrc;
+  for (size_t i = 0; i < targets.size(); ++i) {
+    const int64_t tg = targets[i];
+    const bool full = P.children[8 * (tg / kCells)] >= 0;
+    auto& T = full ? ft : lt;
+    auto& S = full ? fs : ls;
+    auto& M = full ? fm : lm;
+    auto& SRC = full ? fsrc : lsrc;
+    T.push_back(tg);
+    M.push_back((int64_t)SRC.size() + (mid[i] - start[i]));
+    (full ? cs.f_p2p : cs.l_p2p) += start[i + 1] - mid[i];
+    SRC.insert(SRC.end(), sources.begin() + start[i], sources.begin() + start[i + 1]);
+    S.push_back((int64_t)SRC.size());
+  }
+  cs.n_f = (int)ft.size();
+  cs.n_l = (int)lt.size();
+  cs.f_pairs = (int64_t)fsrc.size();
+  cs.l_pairs = (int64_t)lsrc.size();
+  cudaError_t e = cudaSuccess;
+  for (auto [d, v] : {std::pair{&cs.d_ft, &ft}, {&cs.d_fs, &fs}, {&cs.d_fm, &fm}, {&cs.d_fsrc, &fsrc},
+                      {&cs.d_lt, &lt}, {&cs.d_ls, &ls}, {&cs.d_lm, &lm}, {&cs.d_lsrc, &lsrc}})
+    if (e == cudaSuccess) e = upload(d, *v);
+  cs.f = CrossList{cs.d_ft, cs.d_fs, cs.d_fsrc, cs.n_f, cs.d_fm};
+  cs.l = CrossList{cs.d_lt, cs.d_ls, cs.d_lsrc, cs.n_l, cs.d_lm};
+  return e;
+}
+
 }  // namespace
 
 struct octo_fmm {
@@ -52,9 +93,13 @@ struct octo_fmm {
   int *d_interior = nullptr, *d_leaf = nullptr, *d_boundary = nullptr;
   int *d_st_parity = nullptr, *d_st_root = nullptr, *d_st_near = nullptr;
   Kappa* d_kappa = nullptr;
-  int64_t *d_xf_t = nullptr, *d_xf_s = nullptr, *d_xf_src = nullptr;
-  int64_t *d_xl_t = nullptr, *d_xl_s = nullptr, *d_xl_src = nullptr;
-  int64_t *d_xf_m = nullptr, *d_xl_m = nullptr;
+  // cross-level pairs: tabulated point-mass pairs (forward), the general remainder
+  // (forward) and the complete lists (adjoint, uploaded on first use)
+  int64_t *d_xc_t = nullptr, *d_xc_off = nullptr, *d_xc_ent = nullptr;
+  double* d_xc_tab = nullptr;
+  CrossCells xc{};
+  int xc_grid = 0;
+  CrossSet xg, xb;
   // batched interaction phase: strategy (MODE_*), persistent work queue and counter
   int mode = 0, requested_mode = 0;
   int min_blocks = 1, n_sm = 0;
@@ -69,9 +114,6 @@ struct octo_fmm {
   int n_general = 0;
   int *d_cell_ent = nullptr, *d_cell_ent_off = nullptr, *d_bnd_index = nullptr;
   unsigned short* d_bnd_perm = nullptr;
-  int64_t xf_p2p = 0, xl_p2p = 0;  // near (P2P) entries of the cross-level lists
-  int n_xf = 0, n_xl = 0;
-  int64_t xf_pairs = 0, xl_pairs = 0;
 
   // state
   double *d_mp = nullptr, *d_loc = nullptr;
@@ -79,7 +121,6 @@ struct octo_fmm {
   float4* d_kappa32 = nullptr;
   DevTree dt;
   Stencils st;
-  CrossList xf, xl;
   bool forward_done = false;
   bool use_graph = true;
 
@@ -124,14 +165,17 @@ int cuda_fail(octo_fmm* h, cudaError_t e, const char* what) {
 void free_all(octo_fmm* h) {
   void* ptrs[] = {h->d_level,    h->d_parent,  h->d_octant, h->d_children, h->d_nbr,    h->d_leaf_id,
                   h->d_ijk,      h->d_interior, h->d_leaf,  h->d_boundary, h->d_st_parity, h->d_st_root,
-                  h->d_st_near,  h->d_kappa,   h->d_xf_t,   h->d_xf_s,     h->d_xf_src,  h->d_xl_t,
-                  h->d_xl_s,     h->d_xl_src,  h->d_mp,     h->d_loc,      h->d_io,        h->d_mp32,
-                  h->d_xf_m,     h->d_xl_m,    h->d_cell_ent, h->d_cell_ent_off, h->d_bnd_perm,
+                  h->d_st_near,  h->d_kappa,   h->d_xc_t,   h->d_xc_off,   h->d_xc_ent,  h->d_xc_tab,
+                  h->d_mp,       h->d_loc,      h->d_io,        h->d_mp32,
+                  h->d_cell_ent, h->d_cell_ent_off, h->d_bnd_perm,
                   h->d_bnd_index, h->d_mpb,    h->d_locb,
                   h->d_general,  h->d_queue,   h->d_counter, h->d_err,
                   h->d_kappa32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (CrossSet* cs : {&h->xg, &h->xb})
+    for (int64_t* p : {cs->d_ft, cs->d_fs, cs->d_fm, cs->d_fsrc, cs->d_lt, cs->d_ls, cs->d_lm, cs->d_lsrc})
+      if (p) cudaFree(p);
   if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -140,7 +184,7 @@ void free_all(octo_fmm* h) {
 }
 
 // Kinds in solve order; [S_M2L, S_CROSS_LEAF] is the interaction phase.
-enum StageKind { S_P2M, S_M2M, S_M2L, S_CONV, S_PERSIST, S_CROSS_FULL, S_CROSS_LEAF, S_L2L };
+enum StageKind { S_P2M, S_M2M, S_M2L, S_CONV, S_PERSIST, S_CROSS_CELLS, S_CROSS_FULL, S_CROSS_LEAF, S_L2L };
 
 // Interaction strategies (option key 3).
 enum { MODE_AUTO = 0, MODE_PER_KIND = 1, MODE_PERSISTENT = 2 };
@@ -205,13 +249,14 @@ void make_stages(octo_fmm* h) {
         far = P.kernel_pairs[0] * f_int + P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
         near = P.kernel_pairs[2] * kConvFlopsPerPair;
         break;
+      case S_CROSS_CELLS: near = pairs * kConvFlopsPerPair; break;  // float64 in both modes
       case S_CROSS_FULL:
-        far = (pairs - h->xf_p2p) * f_int;
-        near = h->xf_p2p * kP2PFlopsPerPair;
+        far = (pairs - h->xg.f_p2p) * f_int;
+        near = h->xg.f_p2p * kP2PFlopsPerPair;
         break;
       case S_CROSS_LEAF:
-        far = (pairs - h->xl_p2p) * f_leaf;
-        near = h->xl_p2p * kP2PFlopsPerPair;
+        far = (pairs - h->xg.l_p2p) * f_leaf;
+        near = h->xg.l_p2p * kP2PFlopsPerPair;
         break;
       case S_L2L: bytes = cells * 52 * 8; break;                   // own L/X in + L out + parent share
     }
@@ -239,8 +284,13 @@ void make_stages(octo_fmm* h) {
       add(S_CONV, 0, 0, mixed ? "leaf_mixed" : "leaf", P.kernel_pairs[1] + P.kernel_pairs[2] + P.kernel_pairs[3],
           (int64_t)P.leaf_nodes.size() * kCells);
   }
-  if (h->n_xf > 0) add(S_CROSS_FULL, 0, 0, "cross_interior", h->xf_pairs, h->n_xf);
-  if (h->n_xl > 0) add(S_CROSS_LEAF, 0, 0, "cross_leaf", h->xl_pairs, h->n_xl);
+  if (h->xc.n_slices > 0) {
+    int64_t nt = 0;
+    for (int64_t t : P.xc_targets) nt += t >= 0;
+    add(S_CROSS_CELLS, 0, 0, "cross_cells", P.xc_pairs, nt);
+  }
+  if (h->xg.n_f > 0) add(S_CROSS_FULL, 0, 0, "cross_interior", h->xg.f_pairs, h->xg.n_f);
+  if (h->xg.n_l > 0) add(S_CROSS_LEAF, 0, 0, "cross_leaf", h->xg.l_pairs, h->xg.n_l);
   for (int l = 0; l <= P.max_level; ++l)
     if (P.level_start[l + 1] > P.level_start[l])
       add(S_L2L, P.level_start[l], P.level_start[l + 1], "l2l_l" + std::to_string(l), 0,
@@ -293,10 +343,11 @@ cudaError_t enq_stage(octo_fmm* h, const octo_fmm::Stage& st, const double* rho,
     case S_M2L: return launch_interior_items(h->dt, interact_args(h), s);
     case S_CONV: return launch_leaf_items(h->dt, interact_args(h), s);
     case S_PERSIST: return launch_persistent(h->dt, interact_args(h), s);
+    case S_CROSS_CELLS: return launch_cross_cells(h->dt, h->xc, h->d_mp, h->d_loc, h->xc_grid, s);
     case S_CROSS_FULL:
-      return launch_cross_list(h->dt, h->xf, true, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
+      return launch_cross_list(h->dt, h->xg.f, true, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
     case S_CROSS_LEAF:
-      return launch_cross_list(h->dt, h->xl, false, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
+      return launch_cross_list(h->dt, h->xg.l, false, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
     case S_L2L: return launch_l2l(h->dt, st.a, st.b, h->d_mp, h->d_loc, phi, g, h->n_leaf_cells(), s);
   }
   return cudaErrorInvalidValue;
@@ -472,37 +523,11 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
       k32[i] = make_float4((float)kap[i].v[0], (float)kap[i].v[1], (float)kap[i].v[2], (float)kap[i].v[3]);
     up(&h->d_kappa32, k32);
   }
-  // split cross-level targets into interior (full expansion) and leaf targets
-  {
-    std::vector<int64_t> ft, fs, fm, fsrc, lt, ls, lm, lsrc;
-    fs.push_back(0);
-    ls.push_back(0);
-    for (size_t i = 0; i < P.x_targets.size(); ++i) {
-      int64_t tg = P.x_targets[i];
-      bool full = P.children[8 * (tg / kCells)] >= 0;
-      auto& T = full ? ft : lt;
-      auto& S = full ? fs : ls;
-      auto& M = full ? fm : lm;
-      auto& SRC = full ? fsrc : lsrc;
-      T.push_back(tg);
-      M.push_back((int64_t)SRC.size() + (P.x_mid[i] - P.x_start[i]));
-      (full ? h->xf_p2p : h->xl_p2p) += P.x_start[i + 1] - P.x_mid[i];
-      for (int64_t k = P.x_start[i]; k < P.x_start[i + 1]; ++k) SRC.push_back(P.x_sources[k]);
-      S.push_back((int64_t)SRC.size());
-    }
-    h->n_xf = (int)ft.size();
-    h->n_xl = (int)lt.size();
-    h->xf_pairs = (int64_t)fsrc.size();
-    h->xl_pairs = (int64_t)lsrc.size();
-    up(&h->d_xf_t, ft);
-    up(&h->d_xf_s, fs);
-    up(&h->d_xf_m, fm);
-    up(&h->d_xf_src, fsrc);
-    up(&h->d_xl_t, lt);
-    up(&h->d_xl_s, ls);
-    up(&h->d_xl_m, lm);
-    up(&h->d_xl_src, lsrc);
-  }
+  if (e == cudaSuccess) e = upload_cross(P, P.xg_targets, P.xg_start, P.xg_mid, P.xg_sources, h->xg);
+  up(&h->d_xc_t, P.xc_targets);
+  up(&h->d_xc_off, P.xc_slice_off);
+  up(&h->d_xc_ent, P.xc_entries);
+  up(&h->d_xc_tab, P.xc_table);
   up(&h->d_cell_ent, P.cell_ent);
   up(&h->d_cell_ent_off, P.cell_ent_off);
   up(&h->d_bnd_perm, P.bnd_perm);
@@ -543,8 +568,8 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   h->st = Stencils{h->d_st_parity, P.n_st,       h->d_st_root,   (int)P.st_root.size(), h->d_st_near,
                    (int)P.st_near.size(), h->d_kappa, h->d_kappa32, R, RN, h->d_cell_ent, h->d_cell_ent_off,
                    h->d_bnd_perm, h->d_bnd_index};
-  h->xf = CrossList{h->d_xf_t, h->d_xf_s, h->d_xf_src, h->n_xf, h->d_xf_m};
-  h->xl = CrossList{h->d_xl_t, h->d_xl_s, h->d_xl_src, h->n_xl, h->d_xl_m};
+  h->xc = CrossCells{h->d_xc_t, h->d_xc_off, h->d_xc_ent, h->d_xc_tab, (int)(P.xc_slice_off.size() - 1),
+                     (int)(P.xc_table.size() / 4)};
   e = launch_init_leaf(t, h->d_leaf, (int)P.leaf_nodes.size(), h->d_mp, h->d_mp32, h->cap_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap_stream);
   if (e != cudaSuccess) {
@@ -580,6 +605,9 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     if (e == cudaSuccess) e = configure_interact_kernels();
     for (int mb = 1; mb <= 2 && e == cudaSuccess; ++mb)
       e = persistent_blocks_per_sm(precision == OCTO_MIXED, mb, h->st, &h->persist_per_sm[mb]);
+    int xc_per_sm = 0;
+    if (e == cudaSuccess && h->xc.n_slices > 0) e = cross_cells_blocks_per_sm(h->xc, &xc_per_sm);
+    h->xc_grid = h->n_sm * std::max(xc_per_sm, 1);
     if (e != cudaSuccess) {
       std::string m = std::string("work queue setup failed: ") + cudaGetErrorString(e);
       free_all(h);
@@ -693,6 +721,8 @@ int octo_fmm_backward(octo_fmm_t h, const double* dphi, const double* dg, double
     general.insert(general.end(), P.boundary_nodes.begin(), P.boundary_nodes.end());
     h->n_general = (int)general.size();
     e = upload(&h->d_general, general);
+    // the adjoint walks the complete cross-level lists
+    if (e == cudaSuccess) e = upload_cross(P, P.x_targets, P.x_start, P.x_mid, P.x_sources, h->xb);
     // the adjoint kernels keep large per-thread frames: make sure the stack limit covers them
     size_t need = 0, cur = 0;
     if (e == cudaSuccess) e = adjoint_local_bytes(&need);
@@ -723,8 +753,8 @@ int octo_fmm_backward(octo_fmm_t h, const double* dphi, const double* dg, double
   ba.level_start = P.level_start.data();
   ba.max_level = P.max_level;
   ba.st = h->st;
-  ba.xf = h->xf;
-  ba.xl = h->xl;
+  ba.xf = h->xb.f;
+  ba.xl = h->xb.l;
   ba.err = h->d_err;
   e = launch_backward(h->dt, ba, (cudaStream_t)stream);
   return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "backward");

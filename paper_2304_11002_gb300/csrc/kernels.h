@@ -39,6 +39,17 @@ struct CrossList {
   const int64_t* mid;    // per target: first near (P2P) partner; far (M2L) partners precede it
 };
 
+// Cross-level pairs of two leaf cells one level apart, tabulated (SELL-32 layout
+// and entry encoding as built by the planner: see Plan::xc_* in plan.h).
+struct CrossCells {
+  const int64_t* targets;    // [32 * n_slices], -1 for padding lanes
+  const int64_t* slice_off;  // [n_slices + 1]
+  const int64_t* entries;
+  const double* table;       // [n_rows][4]
+  int n_slices;
+  int n_rows;
+};
+
 // ------------------------------------------------------------ tree passes (kernels_fp64.cu)
 // mp32 (may be null): float32 copy of the multipoles for the mixed-precision path.
 cudaError_t launch_init_leaf(const DevTree& t, const int* leaf_nodes, int n_leaf_nodes, double* mp, float* mp32,
@@ -78,6 +89,11 @@ cudaError_t launch_persistent(const DevTree& t, const InteractArgs& a, cudaStrea
 // ------------------------------------------------------------ cross-level pairs (kernels_boundary.cu)
 cudaError_t launch_cross_list(const DevTree& t, const CrossList& xl, bool full, const double* mp, double* loc,
                               bool mixed, cudaStream_t s);
+// Tabulated point-mass pairs, float64 in both precision modes.  grid: a multiple of
+// the SM count (cross_cells_blocks_per_sm gives the resident blocks per SM).
+cudaError_t cross_cells_blocks_per_sm(const CrossCells& xc, int* blocks);
+cudaError_t launch_cross_cells(const DevTree& t, const CrossCells& xc, const double* mp, double* loc, int grid,
+                               cudaStream_t s);
 
 // ------------------------------------------------------------ adjoint (kernels_adjoint.cu)
 struct BackwardArgs {

@@ -1,9 +1,21 @@
 // Cross-level pairs: a leaf cell and a cell of a finer refined region (both
-// directions are listed).  One warp per target cell, lanes striding over its
-// partners, a fixed butterfly reduction at the end (deterministic).  M2L partners
-// come first in each list, then P2P partners (exact point-mass interaction, always
-// float64).  Mixed precision runs the M2L part in float32 with compensated sums,
-// operands scaled to the target's cell width.
+// directions are listed).
+//
+// k_cross_cells: pairs of two leaf cells one level apart.  A leaf cell's multipole
+// is a point mass at the cell centre, so M2L and P2P of such a pair are the same
+// exact term, and the centre offset takes few values (odd multiples of half the
+// finer cell width): the kernel reads the offset's row of a small table (shared
+// memory) and does four float64 fused multiply-adds per pair.  One thread per
+// target cell, targets in SELL-32 slices (a warp's 32 targets have similar partner
+// counts; entry k of the 32 lanes is one coalesced 256-byte load); a persistent
+// grid of warps strides over the slices.  Each target is owned by one thread, so
+// the result is deterministic.
+//
+// k_cross_w (everything else: deeper level differences, refined cells): one warp
+// per target cell, lanes striding over its partners, a fixed butterfly reduction at
+// the end (deterministic).  M2L partners come first in each list, then P2P partners
+// (exact point-mass interaction, always float64).  Mixed precision runs the M2L part
+// in float32 with compensated sums, operands scaled to the target's cell width.
 #include "kernels.h"
 
 namespace octo {
@@ -14,6 +26,55 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+constexpr int kCrossCellsThreads = 256;
+
+__device__ __forceinline__ double flip_sign(double x, int64_t bit) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (bit << 63));
+}
+
+__global__ void __launch_bounds__(kCrossCellsThreads) k_cross_cells(DevTree t, CrossCells xc,
+                                                                    const double* __restrict__ mp,
+                                                                    double* __restrict__ loc) {
+  extern __shared__ double2 tab2[];  // n_rows x 4 doubles
+  const double2* __restrict__ gt = reinterpret_cast<const double2*>(xc.table);
+  for (int i = threadIdx.x; i < 2 * xc.n_rows; i += blockDim.x) tab2[i] = gt[i];
+  __syncthreads();
+  const int64_t NC = t.NC;
+  const int lane = threadIdx.x & 31;
+  const int n_warps = gridDim.x * (blockDim.x >> 5);
+  for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < xc.n_slices; s += n_warps) {
+    const int64_t o0 = xc.slice_off[s];
+    const int64_t width = (xc.slice_off[s + 1] - o0) >> 5;  // a multiple of 4
+    const int64_t* __restrict__ ent = xc.entries + o0 + lane;
+    double S0 = 0.0, S1 = 0.0, S2 = 0.0, S3 = 0.0;
+    for (int64_t k = 0; k < width; k += 4) {
+      int64_t e[4];
+      double m[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) e[u] = __ldcs(ent + 32 * (k + u));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) m[u] = __ldg(mp + (e[u] >> 20));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int row = (int)(e[u] & 0xffff);
+        const double2 a = tab2[2 * row], b = tab2[2 * row + 1];
+        S0 = fma(m[u], a.x, S0);
+        S1 = fma(flip_sign(m[u], (e[u] >> 16) & 1), a.y, S1);
+        S2 = fma(flip_sign(m[u], (e[u] >> 17) & 1), b.x, S2);
+        S3 = fma(flip_sign(m[u], (e[u] >> 18) & 1), b.y, S3);
+      }
+    }
+    const int64_t tg = xc.targets[(int64_t)s * 32 + lane];
+    if (tg >= 0) {
+      const double ih = 1.0 / t.h[t.level[tg >> 9]], ih2 = ih * ih;
+      loc[G_L0 * NC + tg] -= S0 * ih;
+      loc[(G_L1 + 0) * NC + tg] += S1 * ih2;
+      loc[(G_L1 + 1) * NC + tg] += S2 * ih2;
+      loc[(G_L1 + 2) * NC + tg] += S3 * ih2;
+    }
+  }
 }
 
 template <bool FULL, bool MIXED>
@@ -111,6 +172,22 @@ __global__ void __launch_bounds__(128) k_cross_w(DevTree t, CrossList xl, const 
 }
 
 }  // namespace
+
+cudaError_t cross_cells_blocks_per_sm(const CrossCells& xc, int* blocks) {
+  const size_t smem = sizeof(double) * 4 * (size_t)xc.n_rows;
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024) e = cudaFuncSetAttribute(k_cross_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_cross_cells, kCrossCellsThreads, smem);
+  return e;
+}
+
+cudaError_t launch_cross_cells(const DevTree& t, const CrossCells& xc, const double* mp, double* loc, int grid,
+                               cudaStream_t s) {
+  if (xc.n_slices == 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * 4 * (size_t)xc.n_rows;
+  k_cross_cells<<<grid, kCrossCellsThreads, smem, s>>>(t, xc, mp, loc);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cross_list(const DevTree& t, const CrossList& xl, bool full, const double* mp, double* loc,
                               bool mixed, cudaStream_t s) {

@@ -55,6 +55,112 @@ inline Key make_key(int l, int64_t i, int64_t j, int64_t k) {
   return Key{((int64_t)l << 56) | (i << 37) | (j << 18) | k};
 }
 
+// Splits the cross-level pair lists into the tabulated point-mass list (both cells
+// leaves, one level apart) and the general remainder (layouts in plan.h).
+void split_cross_pairs(Plan& P) {
+  int RN = 0;
+  for (int32_t e : P.st_near)
+    for (int k = 0; k < 3; ++k) RN = std::max(RN, std::abs((int)(int8_t)((e >> (8 * k)) & 0xff)));
+  // |v| <= 4 RN + 1 for a pair found from a near offset; rows must fit 16 bits
+  const int na = 2 * RN + 1;
+  const bool table_ok = 2 * (int64_t)na * na * na + 1 < 65536;
+  P.xc_na = na;
+  const int64_t zero_row = 2 * (int64_t)na * na * na;
+  P.xc_table.assign(4 * (zero_row + 1), 0.0);
+  for (int g = 0; g < 2; ++g) {
+    const double s = g == 0 ? 4.0 : 2.0;
+    for (int ax = 0; ax < na; ++ax)
+      for (int ay = 0; ay < na; ++ay)
+        for (int az = 0; az < na; ++az) {
+          const double v[3] = {2.0 * ax + 1, 2.0 * ay + 1, 2.0 * az + 1};
+          const double r = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          double* row = &P.xc_table[4 * (g * (int64_t)na * na * na + (ax * na + ay) * na + az)];
+          row[0] = s / r;
+          for (int k = 0; k < 3; ++k) row[1 + k] = s * s * v[k] / (r * r * r);
+        }
+  }
+  auto cell_index = [&](int64_t c, int64_t I[3]) {
+    const int node = (int)(c / kCells), l = (int)(c % kCells);
+    const int loc[3] = {l & 7, (l >> 3) & 7, l >> 6};
+    for (int a = 0; a < 3; ++a) I[a] = 8 * (int64_t)P.ijk[3 * node + a] + loc[a];
+  };
+  // per target: tabulated entries, general entries (far ones first)
+  std::vector<std::pair<int64_t, int64_t>> by_count;  // (count, slot)
+  std::vector<int64_t> slot_target, tab_start(1, 0), tab_ent;
+  P.xg_targets.clear();
+  P.xg_start.assign(1, 0);
+  P.xg_mid.clear();
+  P.xg_sources.clear();
+  const size_t nt = P.x_targets.size();
+  for (size_t i = 0; i < nt; ++i) {
+    const int64_t tg = P.x_targets[i];
+    const int tn = (int)(tg / kCells), lt = P.level[tn];
+    const bool t_leaf = P.children[8 * tn] < 0;
+    int64_t It[3];
+    cell_index(tg, It);
+    const int64_t tab0 = (int64_t)tab_ent.size();
+    const size_t g0 = P.xg_sources.size();
+    int64_t gmid = -1;
+    for (int64_t e = P.x_start[i]; e < P.x_start[i + 1]; ++e) {
+      const int64_t src = P.x_sources[e];
+      const int sn = (int)(src / kCells), ls = P.level[sn];
+      bool tab = table_ok && t_leaf && P.children[8 * sn] < 0 && std::abs(ls - lt) == 1;
+      int64_t row = 0, signs = 0;
+      if (tab) {
+        int64_t Is[3];
+        cell_index(src, Is);
+        // centres in units of half the finer cell width: fine 2 I + 1, coarse 4 I + 2
+        for (int a = 0; a < 3 && tab; ++a) {
+          const int64_t ct = ls > lt ? 4 * It[a] + 2 : 2 * It[a] + 1;
+          const int64_t cs = ls > lt ? 2 * Is[a] + 1 : 4 * Is[a] + 2;
+          const int64_t v = ct - cs, av = v < 0 ? -v : v;
+          if ((av & 1) == 0 || av > 2 * na - 1) tab = false;
+          row = row * na + (av - 1) / 2;
+          if (v < 0) signs |= 1 << a;
+        }
+        row += (ls > lt ? 0 : 1) * (int64_t)na * na * na;
+      }
+      if (tab) {
+        tab_ent.push_back(src << 20 | signs << 16 | row);
+      } else {
+        if (e >= P.x_mid[i] && gmid < 0) gmid = (int64_t)P.xg_sources.size();
+        P.xg_sources.push_back(src);
+      }
+    }
+    if ((int64_t)tab_ent.size() > tab0) {  // slot k spans tab_ent[tab_start[k], tab_start[k + 1])
+      by_count.push_back({(int64_t)tab_ent.size() - tab0, (int64_t)slot_target.size()});
+      slot_target.push_back(tg);
+      tab_start.push_back((int64_t)tab_ent.size());
+    }
+    if (P.xg_sources.size() > g0) {
+      P.xg_targets.push_back(tg);
+      P.xg_mid.push_back(gmid < 0 ? (int64_t)P.xg_sources.size() : gmid);
+      P.xg_start.push_back((int64_t)P.xg_sources.size());
+    }
+  }
+  P.xc_pairs = (int64_t)tab_ent.size();
+  // SELL-32: sort tabulated targets by decreasing count (ties in list order)
+  std::stable_sort(by_count.begin(), by_count.end(),
+                   [](const std::pair<int64_t, int64_t>& a, const std::pair<int64_t, int64_t>& b) {
+                     return a.first > b.first;
+                   });
+  const int64_t nts = (int64_t)by_count.size(), n_slices = (nts + 31) / 32;
+  P.xc_targets.assign(32 * n_slices, -1);
+  P.xc_slice_off.assign(n_slices + 1, 0);
+  for (int64_t s = 0; s < n_slices; ++s) {
+    int64_t w = by_count[32 * s].first;  // widest target of the slice comes first
+    w = (w + 3) / 4 * 4;
+    P.xc_slice_off[s + 1] = P.xc_slice_off[s] + 32 * w;
+  }
+  P.xc_entries.assign(P.xc_slice_off[n_slices], (int64_t)zero_row);
+  for (int64_t j = 0; j < nts; ++j) {
+    const int64_t s = j / 32, lane = j % 32, slot = by_count[j].second;
+    P.xc_targets[j] = slot_target[slot];
+    const int64_t o = P.xc_slice_off[s] + lane;
+    for (int64_t k = tab_start[slot]; k < tab_start[slot + 1]; ++k) P.xc_entries[o + 32 * (k - tab_start[slot])] = tab_ent[k];
+  }
+}
+
 }  // namespace
 
 int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
@@ -460,6 +566,7 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
   P.x_start.push_back((int64_t)xp.size());
   for (size_t t = 0; t < P.x_targets.size(); ++t)
     if (P.x_mid[t] < 0) P.x_mid[t] = P.x_start[t + 1];
+  split_cross_pairs(P);
 
   P.counts[0] = c_m2l;
   P.counts[1] = c_xm2l;

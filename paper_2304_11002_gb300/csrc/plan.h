@@ -63,6 +63,28 @@ struct Plan {
   std::vector<int64_t> x_mid;            // [n_targets]: first P2P entry (M2L entries come first)
   std::vector<int64_t> x_sources;        // source cell per entry
 
+  // The cross-level pairs split for the forward solve.  Pairs of two leaf cells one
+  // level apart are exact point-mass terms between cell centres whose offset, in
+  // units of half the finer cell width, has odd integer components v; they go to a
+  // tabulated list in SELL-32 layout: targets sorted by decreasing partner count,
+  // 32 targets per slice (padding targets are -1), the entries of a slice stored
+  // interleaved (entry k of lane j at xc_slice_off[s] + 32 k + j; slice widths are
+  // multiples of 4, padded with the zero table row).  Entry = source cell << 20 |
+  // sign bits of v << 16 | table row.  Every other pair stays in the general CSR
+  // lists xg_* (same layout as x_*).
+  std::vector<int64_t> xc_targets;       // [32 * n_slices]
+  std::vector<int64_t> xc_slice_off;     // [n_slices + 1]
+  std::vector<int64_t> xc_entries;
+  // Table rows (4 doubles each): row g * na^3 + (ax * na + ay) * na + az, with
+  // a = (|v| - 1) / 2 per axis and g = 0 when the source is the finer cell (v in
+  // units of h_t / 4), g = 1 when it is the coarser one (units of h_t / 2); row
+  // 2 na^3 is zero.  Row = (s / |v|, s^2 |v_x| / |v|^3, s^2 |v_y| / |v|^3,
+  // s^2 |v_z| / |v|^3) with s = 4 or 2 (the target cell width in those units).
+  std::vector<double> xc_table;
+  int xc_na = 0;
+  int64_t xc_pairs = 0;
+  std::vector<int64_t> xg_targets, xg_start, xg_mid, xg_sources;
+
   // ordered interaction counts: same-level M2L, cross-level M2L, same-level P2P, cross-level P2P
   int64_t counts[4] = {0, 0, 0, 0};
   // same-level pairs per kernel: [0] M2L into interior cells, [1] leaf-leaf M2L,

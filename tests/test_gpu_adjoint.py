@@ -34,13 +34,15 @@ def _gpu_vjp(tree, rho, vphi, vg, precision=binding.OCTO_FP64):
     return drho.cpu().numpy()
 
 
-@pytest.mark.parametrize("which", ["uniform16", "tiny_adaptive"])
+@pytest.mark.parametrize("which", ["uniform16", "tiny_adaptive", "unbalanced"])
 def test_adjoint_matches_oracle_vjp(which):
     if which == "uniform16":
         w = W.uniform16(5)
         tree, rho = w.tree, w.rho.reshape(-1)
     else:
-        tree = W.tree_from_refined({(0, 0, 0, 0), (1, 1, 0, 0)}, 16.0)
+        refined = {(0, 0, 0, 0), (1, 1, 0, 0)} if which == "tiny_adaptive" else \
+            {(0, 0, 0, 0), (1, 0, 0, 0), (2, 1, 1, 1), (3, 3, 3, 3)}
+        tree = W.tree_from_refined(refined, 16.0)
         rho = np.random.default_rng(31).lognormal(size=tree.n_leaf * 512)
     n = rho.size
     rng = np.random.default_rng(32)

@@ -82,6 +82,30 @@ def test_tiny_adaptive_fp64_full():
     assert _rel_g(g, go) <= TOL64
 
 
+def _unbalanced():
+    """A tree that is not 2:1 balanced: level-3 subgrids next to level-1 leaves, so
+    cross-level pairs two levels apart (general cross-level kernel) occur beside the
+    tabulated one-level pairs."""
+    return W.tree_from_refined({(0, 0, 0, 0), (1, 0, 0, 0), (2, 1, 1, 1), (3, 3, 3, 3)}, 16.0)
+
+
+def _stage_names(fmm):
+    return [binding.octo_fmm_stage_info(fmm.handle, i)["name"] for i in range(binding.octo_fmm_stage_count(fmm.handle))]
+
+
+@pytest.mark.parametrize("precision", [binding.OCTO_FP64, binding.OCTO_MIXED])
+def test_unbalanced_tree_full(precision):
+    tree = _unbalanced()
+    rho = np.random.default_rng(12).lognormal(size=(tree.n_leaf, 512))
+    fmm, phi, g = _run(tree, rho, precision)
+    names = _stage_names(fmm)
+    assert "cross_cells" in names and "cross_leaf" in names, names
+    po, go, _ = oracle.fmm(tree, rho)
+    tol = TOL64 if precision == binding.OCTO_FP64 else 1e-6
+    assert _rel_phi(phi, po) <= tol
+    assert _rel_g(g, go) <= tol
+
+
 def _sample(n_cells, k, seed):
     rng = np.random.default_rng(seed)
     idx = np.sort(rng.choice(n_cells, size=min(k, n_cells), replace=False))
