@@ -97,6 +97,7 @@ struct octo_fmm {
   // (forward) and the complete lists (adjoint, uploaded on first use)
   int64_t *d_xc_t = nullptr, *d_xc_off = nullptr, *d_xc_ent = nullptr;
   double* d_xc_tab = nullptr;
+  int* d_xc_counter = nullptr;
   CrossCells xc{};
   int xc_grid = 0;
   CrossSet xg, xb;
@@ -165,7 +166,7 @@ int cuda_fail(octo_fmm* h, cudaError_t e, const char* what) {
 void free_all(octo_fmm* h) {
   void* ptrs[] = {h->d_level,    h->d_parent,  h->d_octant, h->d_children, h->d_nbr,    h->d_leaf_id,
                   h->d_ijk,      h->d_interior, h->d_leaf,  h->d_boundary, h->d_st_parity, h->d_st_root,
-                  h->d_st_near,  h->d_kappa,   h->d_xc_t,   h->d_xc_off,   h->d_xc_ent,  h->d_xc_tab,
+                  h->d_st_near,  h->d_kappa,   h->d_xc_t,   h->d_xc_off,   h->d_xc_ent,  h->d_xc_tab,  h->d_xc_counter,
                   h->d_mp,       h->d_loc,      h->d_io,        h->d_mp32,
                   h->d_cell_ent, h->d_cell_ent_off, h->d_bnd_perm,
                   h->d_bnd_index, h->d_mpb,    h->d_locb,
@@ -528,6 +529,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   up(&h->d_xc_off, P.xc_slice_off);
   up(&h->d_xc_ent, P.xc_entries);
   up(&h->d_xc_tab, P.xc_table);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_xc_counter, sizeof(int));
   up(&h->d_cell_ent, P.cell_ent);
   up(&h->d_cell_ent_off, P.cell_ent_off);
   up(&h->d_bnd_perm, P.bnd_perm);
@@ -569,7 +571,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
                    (int)P.st_near.size(), h->d_kappa, h->d_kappa32, R, RN, h->d_cell_ent, h->d_cell_ent_off,
                    h->d_bnd_perm, h->d_bnd_index};
   h->xc = CrossCells{h->d_xc_t, h->d_xc_off, h->d_xc_ent, h->d_xc_tab, (int)(P.xc_slice_off.size() - 1),
-                     (int)(P.xc_table.size() / 4)};
+                     (int)(P.xc_table.size() / 4), h->d_xc_counter};
   e = launch_init_leaf(t, h->d_leaf, (int)P.leaf_nodes.size(), h->d_mp, h->d_mp32, h->cap_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap_stream);
   if (e != cudaSuccess) {

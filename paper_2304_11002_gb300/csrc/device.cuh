@@ -32,10 +32,12 @@ struct DevTree {
 
 // Float32 copy of the multipoles used by the mixed-precision far field, in units of
 // the cell width h of the cell's level (so that float32 neither overflows nor
-// underflows whatever the physical units):
-//   mp32 [20][NC]  m, x = (X - c_node) / h (c_node = geometric centre of the node),
-//                  Q / h^2, O / h^3.
+// underflows whatever the physical units), cell-major so that one source is five
+// 16-byte loads from one address:
+//   mp32 [NC][20]  m, x = (X - c_node) / h (c_node = geometric centre of the node),
+//                  Q / h^2, O / h^3   (same field order as mp; 80 bytes per cell).
 // Node centres of same-level neighbours differ by exactly 8 h per axis.
+constexpr int kMp32Stride = 20;
 
 // Compensated float32 sum (Kahan): s holds the running sum, c the negative of the
 // rounding error not yet added back; the exact sum is s - c to float32 working

@@ -84,19 +84,55 @@ __device__ __forceinline__ void interior_f64(const DevTree& t, int node, int hal
 
 // ------------------------------------------------------------ interior, float32
 // Positions relative to node centres in cell widths: R = x_A - (x_B + 8 o) for a
-// source in neighbour slot o.
+// source in neighbour slot o.  Accumulation: the pair terms of kAccBlock stencil
+// entries are summed in plain float32 (fused multiply-adds), then each partial sum
+// is added into a float64 accumulator per thread and component kept in shared
+// memory.  A partial sum holds few terms, so its rounding error stays a few float32
+// ulps of the partial, and the float64 sums add no error of their own: the same
+// accuracy as a compensated float32 sum at about a fifth of the instructions, with
+// no accumulator registers beyond the 27 partials.
+constexpr int kAccFields = 27;  // L0, L1(3), L2(6), L3(10), dg(3), W, V(3)
+constexpr int kAccBlock = 32;
+
+__host__ __device__ constexpr size_t interior_smem_bytes() { return sizeof(double) * kAccFields * kThreads; }
+
+// s: this thread's first accumulator; component f at s[f * kThreads]
+__device__ __forceinline__ void flush_partial(Acc<float>& a, double* s) {
+  s[0] += a.L0;
+  for (int i = 0; i < 3; ++i) s[(1 + i) * kThreads] += a.L1[i];
+  for (int i = 0; i < 6; ++i) s[(4 + i) * kThreads] += a.L2[i];
+  for (int i = 0; i < 10; ++i) s[(10 + i) * kThreads] += a.L3[i];
+  for (int i = 0; i < 3; ++i) s[(20 + i) * kThreads] += a.dg[i];
+  s[23 * kThreads] += a.W;
+  for (int i = 0; i < 3; ++i) s[(24 + i) * kThreads] += a.V[i];
+  acc_zero(a);
+}
+
+// One float32 source record (cell-major layout, see device.cuh).
+__device__ __forceinline__ void load_mp32(const float* __restrict__ mp32, int64_t cell, float& m, float x[3],
+                                          float Q[6], float O[10]) {
+  const float4* r = reinterpret_cast<const float4*>(mp32 + cell * kMp32Stride);
+  const float4 v0 = __ldg(r), v1 = __ldg(r + 1), v2 = __ldg(r + 2), v3 = __ldg(r + 3), v4 = __ldg(r + 4);
+  m = v0.x, x[0] = v0.y, x[1] = v0.z, x[2] = v0.w;
+  Q[0] = v1.x, Q[1] = v1.y, Q[2] = v1.z, Q[3] = v1.w, Q[4] = v2.x, Q[5] = v2.y;
+  O[0] = v2.z, O[1] = v2.w, O[2] = v3.x, O[3] = v3.y, O[4] = v3.z, O[5] = v3.w;
+  O[6] = v4.x, O[7] = v4.y, O[8] = v4.z, O[9] = v4.w;
+}
+
+// smem: at least interior_smem_bytes()
 __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int half, const Stencils& st,
-                                             const float* __restrict__ mp32, double* __restrict__ loc) {
+                                             const float* __restrict__ mp32, double* __restrict__ loc,
+                                             unsigned char* smem) {
   int p, zh, a, b, c;
   cell_of(half, threadIdx.x, p, zh, a, b, c);
   const int lvl = t.level[node];
   const int64_t NC = t.NC;
   const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
-  const float xA0 = mp32[(F_X + 0) * NC + tgt], xA1 = mp32[(F_X + 1) * NC + tgt], xA2 = mp32[(F_X + 2) * NC + tgt];
-  float Oh[10], tOh[3];
+  float mA, xA[3], QA[6], Oh[10], tOh[3];
+  load_mp32(mp32, tgt, mA, xA, QA, Oh);
   {
-    const float inv_m = 1.0f / mp32[tgt];
-    for (int i = 0; i < 10; ++i) Oh[i] = mp32[(F_O + i) * NC + tgt] * inv_m;
+    const float inv_m = 1.0f / mA;
+    for (int i = 0; i < 10; ++i) Oh[i] *= inv_m;
     tOh[0] = Oh[0] + Oh[3] + Oh[5];
     tOh[1] = Oh[1] + Oh[6] + Oh[8];
     tOh[2] = Oh[2] + Oh[7] + Oh[9];
@@ -104,32 +140,38 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
   const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
   const int ntab = lvl == 0 ? st.n_root : st.n_st;
   const int* nb = t.nbr + 27 * node;
-  Acc<KF> acc;
-  acc_zero(acc);
-  for (int s = 0; s < ntab; ++s) {
-    int dx, dy, dz;
-    unpack(__ldg(tab + s), dx, dy, dz);
-    const int sa = a + dx, sb = b + dy, sc = c + dz;
-    const int ox = sa >> 3, oy = sb >> 3, oz = sc >> 3;
-    const int snode = __ldg(nb + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
-    if (snode < 0) continue;
-    const int64_t src = (int64_t)snode * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
-    const float R0 = xA0 - (__ldg(mp32 + (F_X + 0) * NC + src) + 8.0f * (float)ox);
-    const float R1 = xA1 - (__ldg(mp32 + (F_X + 1) * NC + src) + 8.0f * (float)oy);
-    const float R2 = xA2 - (__ldg(mp32 + (F_X + 2) * NC + src) + 8.0f * (float)oz);
-    const float m = __ldg(mp32 + src);
-    float Q[6], O[10];
-    for (int i = 0; i < 6; ++i) Q[i] = __ldg(mp32 + (F_Q + i) * NC + src);
-    for (int i = 0; i < 10; ++i) O[i] = __ldg(mp32 + (F_O + i) * NC + src);
-    const float rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
-    m2l_pair<true, true>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, acc);
+  double* sacc = reinterpret_cast<double*>(smem) + threadIdx.x;
+  for (int f = 0; f < kAccFields; ++f) sacc[f * kThreads] = 0.0;
+  Acc<float> part;
+  acc_zero(part);
+  for (int s0 = 0; s0 < ntab; s0 += kAccBlock) {
+    const int s1 = min(s0 + kAccBlock, ntab);
+    for (int s = s0; s < s1; ++s) {
+      int dx, dy, dz;
+      unpack(__ldg(tab + s), dx, dy, dz);
+      const int sa = a + dx, sb = b + dy, sc = c + dz;
+      const int ox = sa >> 3, oy = sb >> 3, oz = sc >> 3;
+      const int snode = __ldg(nb + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
+      if (snode < 0) continue;
+      const int64_t src = (int64_t)snode * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
+      float m, x[3], Q[6], O[10];
+      load_mp32(mp32, src, m, x, Q, O);
+      const float R0 = xA[0] - (x[0] + 8.0f * (float)ox);
+      const float R1 = xA[1] - (x[1] + 8.0f * (float)oy);
+      const float R2 = xA[2] - (x[2] + 8.0f * (float)oz);
+      const float rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
+      m2l_pair<true, true>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, part);
+    }
+    flush_partial(part, sacc);
   }
   Acc<double> d;
-  d.L0 = acc.L0.value();
-  for (int i = 0; i < 3; ++i) d.L1[i] = acc.L1[i].value(), d.dg[i] = acc.dg[i].value(), d.V[i] = acc.V[i].value();
-  for (int i = 0; i < 6; ++i) d.L2[i] = acc.L2[i].value();
-  for (int i = 0; i < 10; ++i) d.L3[i] = acc.L3[i].value();
-  d.W = acc.W.value();
+  d.L0 = sacc[0];
+  for (int i = 0; i < 3; ++i) d.L1[i] = sacc[(1 + i) * kThreads];
+  for (int i = 0; i < 6; ++i) d.L2[i] = sacc[(4 + i) * kThreads];
+  for (int i = 0; i < 10; ++i) d.L3[i] = sacc[(10 + i) * kThreads];
+  for (int i = 0; i < 3; ++i) d.dg[i] = sacc[(20 + i) * kThreads];
+  d.W = sacc[23 * kThreads];
+  for (int i = 0; i < 3; ++i) d.V[i] = sacc[(24 + i) * kThreads];
   acc_finish(d);
   const double ih = 1.0 / t.h[lvl], ih2 = ih * ih, ih3 = ih2 * ih, ih4 = ih2 * ih2;
   loc[G_L0 * NC + tgt] = d.L0 * ih;
@@ -163,7 +205,8 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
   const int* nb = t.nbr + 27 * node;
   T xA0, xA1, xA2;
   if constexpr (MIXED) {
-    xA0 = mp32[(F_X + 0) * NC + tgt], xA1 = mp32[(F_X + 1) * NC + tgt], xA2 = mp32[(F_X + 2) * NC + tgt];
+    xA0 = mp32[tgt * kMp32Stride + F_X + 0], xA1 = mp32[tgt * kMp32Stride + F_X + 1],
+    xA2 = mp32[tgt * kMp32Stride + F_X + 2];
   } else {
     xA0 = mp[(F_X + 0) * NC + tgt], xA1 = mp[(F_X + 1) * NC + tgt], xA2 = mp[(F_X + 2) * NC + tgt];
   }
@@ -180,12 +223,11 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
       const int64_t src = (int64_t)sn * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
       T R0, R1, R2, m, Q[6], O[10], rinv;
       if constexpr (MIXED) {
-        R0 = xA0 - (__ldg(mp32 + (F_X + 0) * NC + src) + 8.0f * (float)ox);
-        R1 = xA1 - (__ldg(mp32 + (F_X + 1) * NC + src) + 8.0f * (float)oy);
-        R2 = xA2 - (__ldg(mp32 + (F_X + 2) * NC + src) + 8.0f * (float)oz);
-        m = __ldg(mp32 + src);
-        for (int i = 0; i < 6; ++i) Q[i] = __ldg(mp32 + (F_Q + i) * NC + src);
-        for (int i = 0; i < 10; ++i) O[i] = __ldg(mp32 + (F_O + i) * NC + src);
+        float x[3];
+        load_mp32(mp32, src, m, x, Q, O);
+        R0 = xA0 - (x[0] + 8.0f * (float)ox);
+        R1 = xA1 - (x[1] + 8.0f * (float)oy);
+        R2 = xA2 - (x[2] + 8.0f * (float)oz);
         rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
       } else {
         R0 = xA0 - __ldg(mp + (F_X + 0) * NC + src);
@@ -238,18 +280,28 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, int half, 
   const int ntab = lvl == 0 ? st.n_root : st.n_st;
   double s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // float64 sums, unit cell width
   if (MIXED) {
+    // far part: plain float32 partial sums of kAccBlock entries merged into
+    // compensated float32 sums (the float64 pipe is kept for the near part)
     KF f0, f1, f2, f3;
     f0 = 0.0f, f1 = 0.0f, f2 = 0.0f, f3 = 0.0f;
     const int base = (a + R) + H * (b + R) + H2 * (c + R);
-    for (int s = 0; s < ntab; ++s) {
-      int dx, dy, dz;
-      unpack(__ldg(tab + s), dx, dy, dz);
-      const float m = halo32[base + dx + H * dy + H2 * dz];
-      const float4 k = __ldg(st.kappa32 + kbase + dx + W * dy + W * W * dz);
-      f0.add(m * k.x);
-      f1.add(m * k.y);
-      f2.add(m * k.z);
-      f3.add(m * k.w);
+    for (int s0 = 0; s0 < ntab; s0 += kAccBlock) {
+      const int s1 = min(s0 + kAccBlock, ntab);
+      float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
+      for (int s = s0; s < s1; ++s) {
+        int dx, dy, dz;
+        unpack(__ldg(tab + s), dx, dy, dz);
+        const float m = halo32[base + dx + H * dy + H2 * dz];
+        const float4 k = __ldg(st.kappa32 + kbase + dx + W * dy + W * W * dz);
+        p0 = fmaf(m, k.x, p0);
+        p1 = fmaf(m, k.y, p1);
+        p2 = fmaf(m, k.z, p2);
+        p3 = fmaf(m, k.w, p3);
+      }
+      f0.add(p0);
+      f1.add(p1);
+      f2.add(p2);
+      f3.add(p3);
     }
     const int baseN = (a + RN) + HN * (b + RN) + HN2 * (c + RN);
     for (int s = 0; s < st.n_near; ++s) {

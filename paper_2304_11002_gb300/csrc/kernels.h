@@ -48,6 +48,7 @@ struct CrossCells {
   const double* table;       // [n_rows][4]
   int n_slices;
   int n_rows;
+  int* counter;              // device scratch: next slice to claim (reset by the launcher)
 };
 
 // ------------------------------------------------------------ tree passes (kernels_fp64.cu)

@@ -8,8 +8,8 @@
 // memory) and does four float64 fused multiply-adds per pair.  One thread per
 // target cell, targets in SELL-32 slices (a warp's 32 targets have similar partner
 // counts; entry k of the 32 lanes is one coalesced 256-byte load); a persistent
-// grid of warps strides over the slices.  Each target is owned by one thread, so
-// the result is deterministic.
+// grid of warps claims slices, widest first, from a counter reset before every
+// launch.  Each target is owned by one thread, so the result is deterministic.
 //
 // k_cross_w (everything else: deeper level differences, refined cells): one warp
 // per target cell, lanes striding over its partners, a fixed butterfly reduction at
@@ -43,17 +43,28 @@ __global__ void __launch_bounds__(kCrossCellsThreads) k_cross_cells(DevTree t, C
   __syncthreads();
   const int64_t NC = t.NC;
   const int lane = threadIdx.x & 31;
-  const int n_warps = gridDim.x * (blockDim.x >> 5);
-  for (int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < xc.n_slices; s += n_warps) {
+  for (;;) {
+    // the next slice, claimed by the warp (slices are sorted widest first)
+    int s = 0;
+    if (lane == 0) s = atomicAdd(xc.counter, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= xc.n_slices) return;
     const int64_t o0 = xc.slice_off[s];
     const int64_t width = (xc.slice_off[s + 1] - o0) >> 5;  // a multiple of 4
     const int64_t* __restrict__ ent = xc.entries + o0 + lane;
     double S0 = 0.0, S1 = 0.0, S2 = 0.0, S3 = 0.0;
+    int64_t en[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) en[u] = __ldcs(ent + 32 * u);
     for (int64_t k = 0; k < width; k += 4) {
       int64_t e[4];
       double m[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) e[u] = __ldcs(ent + 32 * (k + u));
+      for (int u = 0; u < 4; ++u) e[u] = en[u];
+      if (k + 4 < width) {  // next group's entries, in flight during this group
+#pragma unroll
+        for (int u = 0; u < 4; ++u) en[u] = __ldcs(ent + 32 * (k + 4 + u));
+      }
 #pragma unroll
       for (int u = 0; u < 4; ++u) m[u] = __ldg(mp + (e[u] >> 20));
 #pragma unroll
@@ -185,6 +196,8 @@ cudaError_t launch_cross_cells(const DevTree& t, const CrossCells& xc, const dou
                                cudaStream_t s) {
   if (xc.n_slices == 0) return cudaSuccess;
   const size_t smem = sizeof(double) * 4 * (size_t)xc.n_rows;
+  cudaError_t e = cudaMemsetAsync(xc.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   k_cross_cells<<<grid, kCrossCellsThreads, smem, s>>>(t, xc, mp, loc);
   return cudaGetLastError();
 }

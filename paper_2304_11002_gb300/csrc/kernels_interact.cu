@@ -8,6 +8,8 @@
 //    SMs and the tail of one kind overlaps the other.  The counter is reset by a
 //    memset issued before every launch; no block ever waits for another.
 // The autotuner in capi.cu times both on the actual tree and keeps the faster.
+#include <algorithm>
+
 #include "items.cuh"
 
 namespace octo {
@@ -15,13 +17,14 @@ namespace octo {
 namespace {
 
 template <bool MIXED>
-__global__ void __launch_bounds__(items::kThreads) k_interior_items(DevTree t, const int* __restrict__ nodes,
+__global__ void __launch_bounds__(items::kThreads, MIXED ? 3 : 1) k_interior_items(DevTree t, const int* __restrict__ nodes,
                                                                      Stencils st, const double* __restrict__ mp,
                                                                      const float* __restrict__ mp32,
                                                                      double* __restrict__ loc) {
+  extern __shared__ __align__(16) unsigned char smem[];
   const int node = nodes[blockIdx.x >> 1];
   if (MIXED)
-    items::interior_f32(t, node, blockIdx.x & 1, st, mp32, loc);
+    items::interior_f32(t, node, blockIdx.x & 1, st, mp32, loc, smem);
   else
     items::interior_f64(t, node, blockIdx.x & 1, st, mp, loc);
 }
@@ -54,7 +57,7 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
       items::leaf_item<MIXED>(t, node, half, st, mp, mp32, loc, smem);
     } else {
       if (MIXED)
-        items::interior_f32(t, node, half, st, mp32, loc);
+        items::interior_f32(t, node, half, st, mp32, loc, smem);
       else
         items::interior_f64(t, node, half, st, mp, loc);
     }
@@ -63,9 +66,15 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
 
 // Resident blocks per SM of a persistent variant (sets its shared-memory limit);
 // called once per handle, outside any stream capture.
+// Dynamic shared memory of the persistent kernel: the larger of the two items' needs.
+size_t persistent_smem_bytes(const Stencils& st, bool mixed) {
+  const size_t leaf = items::leaf_smem_bytes(st, mixed);
+  return mixed ? std::max(leaf, items::interior_smem_bytes()) : leaf;
+}
+
 template <bool MIXED, int MINB>
 cudaError_t persistent_occupancy(const Stencils& st, int* per_sm) {
-  const size_t smem = items::leaf_smem_bytes(st, MIXED);
+  const size_t smem = persistent_smem_bytes(st, MIXED);
   cudaError_t e = cudaFuncSetAttribute(k_persistent<MIXED, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -76,7 +85,7 @@ cudaError_t persistent_occupancy(const Stencils& st, int* per_sm) {
 
 template <bool MIXED, int MINB>
 cudaError_t persistent_launch(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
-  const size_t smem = items::leaf_smem_bytes(a.st, MIXED);
+  const size_t smem = persistent_smem_bytes(a.st, MIXED);
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_persistent<MIXED, MINB><<<a.grid, items::kThreads, smem, s>>>(t, a.queue, a.n_items, a.counter, a.st, a.mp,
@@ -91,13 +100,17 @@ cudaError_t configure_interact_kernels() {
   const int big = 200 * 1024;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leaf_items<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leaf_items<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_interior_items<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)items::interior_smem_bytes());
   return e;
 }
 
 cudaError_t launch_interior_items(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
   if (a.n_interior == 0) return cudaSuccess;
   if (a.mixed)
-    k_interior_items<true><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp, a.mp32, a.loc);
+    k_interior_items<true><<<2 * a.n_interior, items::kThreads, items::interior_smem_bytes(), s>>>(
+        t, a.interior, a.st, a.mp, a.mp32, a.loc);
   else
     k_interior_items<false><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp, a.mp32, a.loc);
   return cudaGetLastError();
