@@ -209,6 +209,39 @@ def time_solver(w, precision, steps, warmup, torch, flush, stream, strategy="aut
     return fmm, info, np.array(step_ms), np.array(stage_ms), launches, (rho, phi, g)
 
 
+def roofline_of(info, mean_stage_ms, peaks):
+    """Roofline of the stage that takes longest (CUDA-event time per solve)."""
+    k = int(np.argmax(mean_stage_ms))
+    st = info[k]
+    dur_s = mean_stage_ms[k] / 1e3
+    if st["flops"] > 0:
+        # A stage may mix float32 (far field) and float64 (near field) work: the
+        # binding unit is the one whose work takes longer at its peak.
+        f64, f32 = st["flops64"], st["flops"] - st["flops64"]
+        fp32_bound = f32 / PEAK_FP32_TFLOPS > f64 / PEAK_FP64_TFLOPS
+        peak = PEAK_FP32_TFLOPS if fp32_bound else PEAK_FP64_TFLOPS
+        achieved = (f32 if fp32_bound else f64) / dur_s / 1e12
+        return {"bound": "alu", "kernel": st["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "pipe": "fp32" if fp32_bound else "fp64",
+                "other_pipe_frac": ((f64 / dur_s / 1e12) / PEAK_FP64_TFLOPS if fp32_bound else
+                                    (f32 / dur_s / 1e12) / PEAK_FP32_TFLOPS),
+                "peak_source": ("derived: 152 SMs x %s x 2.07 GHz" % ("256 fp32 flop/clk" if fp32_bound else
+                                                                      "4 fp64 flop/clk (1.25 TFLOP/s nominal)"))}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = st["bytes"] / dur_s / 1e9
+    return {"bound": "hbm", "kernel": st["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": "measured" if peaks else "fallback"}
+
+
+def interaction_fp64_frac(info, mean_stage_ms):
+    """float64 flop rate of all interaction stages together (their float64 flops over
+    their summed event time) as a fraction of the float64 peak."""
+    f64 = sum(st["flops64"] for st in info if st["pairs"] > 0)
+    ms = sum(float(mean_stage_ms[i]) for i, st in enumerate(info) if st["pairs"] > 0)
+    return f64 / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS if ms > 0 else None
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -246,29 +279,7 @@ def run_ours(args):
 
     # dominant kernel of the step and its roofline
     mean_stage = stage_ms.mean(axis=0)
-    k = int(np.argmax(mean_stage))
-    st = info[k]
-    dur_s = mean_stage[k] / 1e3
-    peaks = _measured_peaks()
-    if st["flops"] > 0:
-        # A stage may mix float32 (far field) and float64 (near field) work: the
-        # binding unit is the one whose work takes longer at its peak.
-        f64, f32 = st["flops64"], st["flops"] - st["flops64"]
-        fp32_bound = f32 / PEAK_FP32_TFLOPS > f64 / PEAK_FP64_TFLOPS
-        peak = PEAK_FP32_TFLOPS if fp32_bound else PEAK_FP64_TFLOPS
-        achieved = (f32 if fp32_bound else f64) / dur_s / 1e12
-        roof = {"bound": "alu", "kernel": st["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "pipe": "fp32" if fp32_bound else "fp64",
-                "other_pipe_frac": ((f64 / dur_s / 1e12) / PEAK_FP64_TFLOPS if fp32_bound else
-                                    (f32 / dur_s / 1e12) / PEAK_FP32_TFLOPS),
-                "peak_source": ("derived: 152 SMs x %s x 2.07 GHz" % ("256 fp32 flop/clk" if fp32_bound else
-                                                                      "4 fp64 flop/clk (1.25 TFLOP/s nominal)"))}
-    else:
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        achieved = st["bytes"] / dur_s / 1e9
-        roof = {"bound": "hbm", "kernel": st["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": "measured" if peaks else "fallback"}
+    roof = roofline_of(info, mean_stage, _measured_peaks())
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     nlc = fmm.n_leaf_cells
@@ -300,7 +311,9 @@ def run_ours(args):
                                                    stream, args.strategy)
         m64 = st_ms.mean(axis=0)
         fp64 = {"value": n_inter / (float(np.mean(s_ms)) / 1e3), "ms_per_step": float(np.mean(s_ms)),
-                "stages_ms": {info64[i]["name"]: round(float(m64[i]), 4) for i in range(len(info64))}}
+                "stages_ms": {info64[i]["name"]: round(float(m64[i]), 4) for i in range(len(info64))},
+                "roofline": roofline_of(info64, m64, _measured_peaks()),
+                "interaction_fp64_frac": interaction_fp64_frac(info64, m64)}
 
     if rank != 0:
         return 0

@@ -114,6 +114,7 @@ struct octo_fmm {
   int* d_general = nullptr;
   int n_general = 0;
   int *d_cell_ent = nullptr, *d_cell_ent_off = nullptr, *d_bnd_index = nullptr;
+  int2 *d_leaf_far = nullptr, *d_leaf_root = nullptr, *d_leaf_near = nullptr;
   unsigned short* d_bnd_perm = nullptr;
 
   // state
@@ -171,6 +172,7 @@ void free_all(octo_fmm* h) {
                   h->d_cell_ent, h->d_cell_ent_off, h->d_bnd_perm,
                   h->d_bnd_index, h->d_mpb,    h->d_locb,
                   h->d_general,  h->d_queue,   h->d_counter, h->d_err,
+                  h->d_leaf_far, h->d_leaf_root, h->d_leaf_near,
                   h->d_kappa32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -567,9 +569,24 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   int RN = 0;
   for (int32_t v : P.st_near)
     for (int k = 0; k < 3; ++k) RN = std::max(RN, std::abs((int)(int8_t)((v >> (8 * k)) & 0xff)));
+  {  // leaf-item tables (halo offsets and kernel rows per parity class and entry)
+    const int ns = P.n_st, nr = (int)P.st_root.size(), nn = (int)P.st_near.size();
+    std::vector<int2> lf((size_t)8 * ns), lr((size_t)8 * nr), ln((size_t)8 * nn);
+    build_leaf_tables(P.st_parity.data(), ns, P.st_root.data(), nr, P.st_near.data(), nn, R, RN,
+                      precision == OCTO_MIXED, lf.data(), lr.data(), ln.data());
+    e = upload(&h->d_leaf_far, lf);
+    if (e == cudaSuccess) e = upload(&h->d_leaf_root, lr);
+    if (e == cudaSuccess) e = upload(&h->d_leaf_near, ln);
+    if (e != cudaSuccess) {
+      std::string m = std::string("device setup failed: ") + cudaGetErrorString(e);
+      free_all(h);
+      delete h;
+      return create_fail(e == cudaErrorMemoryAllocation ? OCTO_ENOMEM : OCTO_ECUDA, m);
+    }
+  }
   h->st = Stencils{h->d_st_parity, P.n_st,       h->d_st_root,   (int)P.st_root.size(), h->d_st_near,
                    (int)P.st_near.size(), h->d_kappa, h->d_kappa32, R, RN, h->d_cell_ent, h->d_cell_ent_off,
-                   h->d_bnd_perm, h->d_bnd_index};
+                   h->d_bnd_perm, h->d_bnd_index, h->d_leaf_far, h->d_leaf_root, h->d_leaf_near};
   h->xc = CrossCells{h->d_xc_t, h->d_xc_off, h->d_xc_ent, h->d_xc_tab, (int)(P.xc_slice_off.size() - 1),
                      (int)(P.xc_table.size() / 4), h->d_xc_counter};
   e = launch_init_leaf(t, h->d_leaf, (int)P.leaf_nodes.size(), h->d_mp, h->d_mp32, h->cap_stream);
@@ -580,24 +597,39 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     delete h;
     return create_fail(OCTO_ECUDA, m);
   }
-  // persistent work queue: interior items of the root, then of the other levels,
-  // then leaf items with refined neighbours, then the other leaf items
+  // persistent work queue.  Interior items of the root first (the largest), then of
+  // the other levels; leaf items with refined neighbours before the other leaf items.
+  // Float64: all interior items, then all leaf items.  Mixed precision: the two lists
+  // merged in proportion (each prefix of the queue holds the same fraction of both),
+  // so that float32-bound interior items and float64-bound leaf items (their
+  // near field) run side by side on every SM and use both pipes.
   {
-    std::vector<int32_t> q;
-    auto push = [&](int node, int kind) {
-      q.push_back((node << 2) | (kind << 1) | 0);
-      q.push_back((node << 2) | (kind << 1) | 1);
+    std::vector<int32_t> qi, ql, q;
+    auto push = [](std::vector<int32_t>& v, int node, int kind) {  // interior: two halves; leaf: whole node
+      v.push_back((node << 2) | (kind << 1) | 0);
+      if (kind == 0) v.push_back((node << 2) | (kind << 1) | 1);
     };
     for (int k : P.interior_nodes)
-      if (P.level[k] == 0) push(k, 0);
+      if (P.level[k] == 0) push(qi, k, 0);
     for (int k : P.interior_nodes)
-      if (P.level[k] != 0) push(k, 0);
+      if (P.level[k] != 0) push(qi, k, 0);
     std::vector<char> bnd(P.n_nodes, 0);
     for (int k : P.boundary_nodes) bnd[k] = 1;
     for (int k : P.leaf_nodes)
-      if (bnd[k]) push(k, 1);
+      if (bnd[k]) push(ql, k, 1);
     for (int k : P.leaf_nodes)
-      if (!bnd[k]) push(k, 1);
+      if (!bnd[k]) push(ql, k, 1);
+    if (precision == OCTO_MIXED) {
+      size_t i = 0, l = 0;
+      while (i < qi.size() || l < ql.size()) {
+        // take an interior item while its list is not ahead: i / |qi| <= l / |ql|
+        const bool take_i = l == ql.size() || (i < qi.size() && i * ql.size() <= l * qi.size());
+        q.push_back(take_i ? qi[i++] : ql[l++]);
+      }
+    } else {
+      q = qi;
+      q.insert(q.end(), ql.begin(), ql.end());
+    }
     h->n_items = (int)q.size();
     e = upload(&h->d_queue, q);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_counter, sizeof(int));

@@ -19,7 +19,7 @@ namespace items {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ void cell_of(int half, int tid, int& p, int& zh, int& a, int& b, int& c) {
+__host__ __device__ __forceinline__ void cell_of(int half, int tid, int& p, int& zh, int& a, int& b, int& c) {
   const int w = tid >> 5, lane = tid & 31;
   p = half * 4 + (w >> 1);
   zh = w & 1;
@@ -29,7 +29,7 @@ __device__ __forceinline__ void cell_of(int half, int tid, int& p, int& zh, int&
   c = 2 * (q >> 4) + (p >> 2);
 }
 
-__device__ __forceinline__ void unpack(int e, int& dx, int& dy, int& dz) {
+__host__ __device__ __forceinline__ void unpack(int e, int& dx, int& dy, int& dz) {
   dx = (int)(int8_t)(e & 0xff);
   dy = (int)(int8_t)((e >> 8) & 0xff);
   dz = (int)(int8_t)((e >> 16) & 0xff);
@@ -85,26 +85,23 @@ __device__ __forceinline__ void interior_f64(const DevTree& t, int node, int hal
 // ------------------------------------------------------------ interior, float32
 // Positions relative to node centres in cell widths: R = x_A - (x_B + 8 o) for a
 // source in neighbour slot o.  Accumulation: the pair terms of kAccBlock stencil
-// entries are summed in plain float32 (fused multiply-adds), then each partial sum
-// is added into a float64 accumulator per thread and component kept in shared
-// memory.  A partial sum holds few terms, so its rounding error stays a few float32
-// ulps of the partial, and the float64 sums add no error of their own: the same
-// accuracy as a compensated float32 sum at about a fifth of the instructions, with
-// no accumulator registers beyond the 27 partials.
-constexpr int kAccFields = 27;  // L0, L1(3), L2(6), L3(10), dg(3), W, V(3)
+// entries are summed in plain float32 (fused multiply-adds); each partial sum then
+// gets its deferred Kronecker parts (acc_finish is linear) and is added into the
+// target's float64 local expansion in global memory, which stays in L2 and is
+// touched once per block of entries.  A partial holds few terms, so its rounding
+// error stays a few float32 ulps of the partial, and the float64 sums add no error
+// of their own: the accuracy of a compensated float32 sum at about a fifth of the
+// instructions, with no accumulator registers beyond the 27 partials and no shared
+// memory (which is left to L1, where the source records are cached).
 constexpr int kAccBlock = 32;
 
-__host__ __device__ constexpr size_t interior_smem_bytes() { return sizeof(double) * kAccFields * kThreads; }
-
-// s: this thread's first accumulator; component f at s[f * kThreads]
-__device__ __forceinline__ void flush_partial(Acc<float>& a, double* s) {
-  s[0] += a.L0;
-  for (int i = 0; i < 3; ++i) s[(1 + i) * kThreads] += a.L1[i];
-  for (int i = 0; i < 6; ++i) s[(4 + i) * kThreads] += a.L2[i];
-  for (int i = 0; i < 10; ++i) s[(10 + i) * kThreads] += a.L3[i];
-  for (int i = 0; i < 3; ++i) s[(20 + i) * kThreads] += a.dg[i];
-  s[23 * kThreads] += a.W;
-  for (int i = 0; i < 3; ++i) s[(24 + i) * kThreads] += a.V[i];
+__device__ __forceinline__ void flush_partial(Acc<float>& a, double* __restrict__ loc, int64_t NC, int64_t tgt) {
+  acc_finish(a);
+  loc[G_L0 * NC + tgt] += a.L0;
+  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] += a.L1[i];
+  for (int i = 0; i < 6; ++i) loc[(G_L2 + i) * NC + tgt] += a.L2[i];
+  for (int i = 0; i < 10; ++i) loc[(G_L3 + i) * NC + tgt] += a.L3[i];
+  for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] += a.dg[i];
   acc_zero(a);
 }
 
@@ -119,10 +116,8 @@ __device__ __forceinline__ void load_mp32(const float* __restrict__ mp32, int64_
   O[6] = v4.x, O[7] = v4.y, O[8] = v4.z, O[9] = v4.w;
 }
 
-// smem: at least interior_smem_bytes()
 __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int half, const Stencils& st,
-                                             const float* __restrict__ mp32, double* __restrict__ loc,
-                                             unsigned char* smem) {
+                                             const float* __restrict__ mp32, double* __restrict__ loc) {
   int p, zh, a, b, c;
   cell_of(half, threadIdx.x, p, zh, a, b, c);
   const int lvl = t.level[node];
@@ -140,8 +135,7 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
   const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
   const int ntab = lvl == 0 ? st.n_root : st.n_st;
   const int* nb = t.nbr + 27 * node;
-  double* sacc = reinterpret_cast<double*>(smem) + threadIdx.x;
-  for (int f = 0; f < kAccFields; ++f) sacc[f * kThreads] = 0.0;
+  for (int f = 0; f < N_LOC; ++f) loc[f * NC + tgt] = 0.0;
   Acc<float> part;
   acc_zero(part);
   for (int s0 = 0; s0 < ntab; s0 += kAccBlock) {
@@ -162,32 +156,66 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
       const float rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
       m2l_pair<true, true>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, part);
     }
-    flush_partial(part, sacc);
+    flush_partial(part, loc, NC, tgt);
   }
-  Acc<double> d;
-  d.L0 = sacc[0];
-  for (int i = 0; i < 3; ++i) d.L1[i] = sacc[(1 + i) * kThreads];
-  for (int i = 0; i < 6; ++i) d.L2[i] = sacc[(4 + i) * kThreads];
-  for (int i = 0; i < 10; ++i) d.L3[i] = sacc[(10 + i) * kThreads];
-  for (int i = 0; i < 3; ++i) d.dg[i] = sacc[(20 + i) * kThreads];
-  d.W = sacc[23 * kThreads];
-  for (int i = 0; i < 3; ++i) d.V[i] = sacc[(24 + i) * kThreads];
-  acc_finish(d);
+  // unit cell width -> physical units: L_n scales with h^-(n+1), dg with h^-2
   const double ih = 1.0 / t.h[lvl], ih2 = ih * ih, ih3 = ih2 * ih, ih4 = ih2 * ih2;
-  loc[G_L0 * NC + tgt] = d.L0 * ih;
-  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = d.L1[i] * ih2;
-  for (int i = 0; i < 6; ++i) loc[(G_L2 + i) * NC + tgt] = d.L2[i] * ih3;
-  for (int i = 0; i < 10; ++i) loc[(G_L3 + i) * NC + tgt] = d.L3[i] * ih4;
-  for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] = d.dg[i] * ih2;
+  loc[G_L0 * NC + tgt] *= ih;
+  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] *= ih2;
+  for (int i = 0; i < 6; ++i) loc[(G_L2 + i) * NC + tgt] *= ih3;
+  for (int i = 0; i < 10; ++i) loc[(G_L3 + i) * NC + tgt] *= ih4;
+  for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] *= ih2;
 }
 
 // ------------------------------------------------------------ leaf item
-// Shared memory: float64 halo of radius R (float64 path), or float32 halo of
-// radius R plus float64 halo of the near radius (mixed path).
-// (at least 512 x 7 doubles: the boundary results are exchanged through it).
+// The mass halo of a leaf node (the node's 8^3 cells and a border of width r) is
+// kept in shared memory split by cell parity: halo coordinate h in [0, 8 + 2r) per
+// axis goes to parity block (hx & 1) + 2 (hy & 1) + 4 (hz & 1), position
+// (hx >> 1, hy >> 1, hz >> 1) in a G^3 sub-grid (G = 4 + r) with row pitch PY and
+// plane pitch PZ.  The 32 lanes of a warp hold one parity class of targets (cells
+// (2i + pa, 2j + pb, 2k + pc), i, j < 4, k < 2), so for any stencil offset their
+// sources are (i + u, j + v, k + w) in one parity block: lane offsets i + PY j + PZ k.
+// Far halo: PY = 12 (mod 32) and PZ = 16 (mod 32) make the 32 float32 loads hit 32
+// distinct banks, and the 16 float64 loads of each half-warp 16 distinct bank
+// pairs.  The near float64 halo of the mixed path is dense (small radius).
+struct HaloGeom {
+  int r, G, PY, PZ, PQ;  // border, sub-grid extent, row pitch, plane pitch, parity block size
+};
+
+__host__ __device__ inline HaloGeom far_geom(int r) {
+  HaloGeom g;
+  g.r = r;
+  g.G = 4 + r;
+  g.PY = 12;
+  while (g.PY < g.G) g.PY += 32;
+  g.PZ = 16;
+  while (g.PZ < g.G * g.PY) g.PZ += 32;
+  g.PQ = g.G * g.PZ;
+  return g;
+}
+
+__host__ __device__ inline HaloGeom near_geom(int r) {
+  HaloGeom g;
+  g.r = r;
+  g.G = 4 + r;
+  g.PY = g.G;
+  g.PZ = g.G * g.G;
+  g.PQ = g.G * g.PZ;
+  return g;
+}
+
+// Offset of halo position (hx, hy, hz) from the origin of the halo.
+__host__ __device__ inline int halo_index(const HaloGeom& g, int hx, int hy, int hz) {
+  return ((hx & 1) + 2 * (hy & 1) + 4 * (hz & 1)) * g.PQ + (hx >> 1) + g.PY * (hy >> 1) + g.PZ * (hz >> 1);
+}
+
+// Shared memory of a leaf item: the far halo (float32 in the mixed path, float64
+// otherwise), the near float64 halo (mixed path), and at least 512 x 7 doubles
+// (the boundary results are exchanged through it).
 __host__ __device__ inline size_t leaf_smem_bytes(const Stencils& st, bool mixed) {
-  const size_t H = 8 + 2 * st.radius, HN = 8 + 2 * st.near_radius;
-  const size_t halo = mixed ? sizeof(double) * HN * HN * HN + sizeof(float) * H * H * H : sizeof(double) * H * H * H;
+  const HaloGeom gf = far_geom(st.radius), gn = near_geom(st.near_radius);
+  const size_t halo = mixed ? sizeof(float) * 8 * (size_t)gf.PQ + sizeof(double) * 8 * (size_t)gn.PQ
+                            : sizeof(double) * 8 * (size_t)gf.PQ;
   return halo > sizeof(double) * 512 * 7 ? halo : sizeof(double) * 512 * 7;
 }
 
@@ -243,134 +271,167 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
   }
 }
 
+// One leaf node per block (both halves): stage the halo once, then every thread
+// computes its cell of each half.  Mixed path: after every block of kAccBlock far
+// entries (float32) the thread takes its share of the near entries (float64), so
+// that each warp keeps both the float32 and the float64 pipe busy.
 template <bool MIXED>
-__device__ __forceinline__ void leaf_item(const DevTree& t, int node, int half, const Stencils& st,
+__device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Stencils& st,
                                           const double* __restrict__ mp, const float* __restrict__ mp32,
                                           double* __restrict__ loc, unsigned char* smem) {
-  const int R = st.radius, H = 8 + 2 * R, H2 = H * H, W = 2 * R + 1;
-  const int RN = st.near_radius, HN = 8 + 2 * RN, HN2 = HN * HN;
-  const int* nb = t.nbr + 27 * node;
-  double* halo64 = reinterpret_cast<double*>(smem);
-  float* halo32 = reinterpret_cast<float*>(smem + sizeof(double) * HN2 * HN);
-  bool refined_nbr = false;
-  for (int o = 0; o < 27; ++o) {
-    const int sn = nb[o];
-    refined_nbr |= sn >= 0 && t.children[8 * sn] >= 0;
+  const HaloGeom gf = far_geom(st.radius), gn = near_geom(st.near_radius);
+  const int R = gf.r, H = 2 * gf.G, RN = gn.r;
+  __shared__ int nleaf[27];  // leaf same-level neighbour (or the node itself), else -1
+  __shared__ int any_refined;
+  __syncthreads();  // the previous item may still read shared memory
+  if (threadIdx.x < 27) {
+    const int sn = t.nbr[27 * node + threadIdx.x];
+    const bool leaf = sn >= 0 && t.children[8 * sn] < 0;
+    nleaf[threadIdx.x] = leaf ? sn : -1;
   }
-  __syncthreads();  // the previous item may still read the halo
-  for (int i = threadIdx.x; i < H2 * H; i += blockDim.x) {
-    const int hx = i % H - R, hy = (i / H) % H - R, hz = i / H2 - R;
-    const int sn = nb[((hx >> 3) + 1) + 3 * ((hy >> 3) + 1) + 9 * ((hz >> 3) + 1)];
-    double m = 0.0;
-    if (sn >= 0 && t.children[8 * sn] < 0) m = mp[(int64_t)sn * 512 + (hx & 7) + 8 * (hy & 7) + 64 * (hz & 7)];
+  if (threadIdx.x == 0) {
+    int any = 0;
+    for (int o = 0; o < 27; ++o) {
+      const int sn = t.nbr[27 * node + o];
+      any |= sn >= 0 && t.children[8 * sn] >= 0;
+    }
+    any_refined = any;
+  }
+  __syncthreads();
+  float* halo32 = reinterpret_cast<float*>(smem);
+  double* halo64 = MIXED ? reinterpret_cast<double*>(smem + sizeof(float) * 8 * (size_t)gf.PQ)
+                         : reinterpret_cast<double*>(smem);
+  for (int i = threadIdx.x; i < H * H * H; i += blockDim.x) {
+    const int hx = i % H, hy = (i / H) % H, hz = i / (H * H);
+    const int x = hx - R, y = hy - R, z = hz - R;
+    const int sn = nleaf[((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1)];
+    const double m = sn >= 0 ? mp[(int64_t)sn * 512 + (x & 7) + 8 * (y & 7) + 64 * (z & 7)] : 0.0;
     if (MIXED) {
-      halo32[i] = (float)m;
-      if (hx >= -RN && hx < 8 + RN && hy >= -RN && hy < 8 + RN && hz >= -RN && hz < 8 + RN)
-        halo64[(hx + RN) + HN * (hy + RN) + HN2 * (hz + RN)] = m;
+      halo32[halo_index(gf, hx, hy, hz)] = (float)m;
+      if (x >= -RN && x < 8 + RN && y >= -RN && y < 8 + RN && z >= -RN && z < 8 + RN)
+        halo64[halo_index(gn, x + RN, y + RN, z + RN)] = m;
     } else {
-      reinterpret_cast<double*>(smem)[i] = m;
+      halo64[halo_index(gf, hx, hy, hz)] = m;
     }
   }
   __syncthreads();
-  int p, zh, a, b, c;
-  cell_of(half, threadIdx.x, p, zh, a, b, c);
   const int lvl = t.level[node];
-  const int kbase = R + W * R + W * W * R;
-  const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
-  const int ntab = lvl == 0 ? st.n_root : st.n_st;
-  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // float64 sums, unit cell width
-  if (MIXED) {
-    // far part: plain float32 partial sums of kAccBlock entries merged into
-    // compensated float32 sums (the float64 pipe is kept for the near part)
-    KF f0, f1, f2, f3;
-    f0 = 0.0f, f1 = 0.0f, f2 = 0.0f, f3 = 0.0f;
-    const int base = (a + R) + H * (b + R) + H2 * (c + R);
-    for (int s0 = 0; s0 < ntab; s0 += kAccBlock) {
-      const int s1 = min(s0 + kAccBlock, ntab);
-      float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
-      for (int s = s0; s < s1; ++s) {
-        int dx, dy, dz;
-        unpack(__ldg(tab + s), dx, dy, dz);
-        const float m = halo32[base + dx + H * dy + H2 * dz];
-        const float4 k = __ldg(st.kappa32 + kbase + dx + W * dy + W * W * dz);
-        p0 = fmaf(m, k.x, p0);
-        p1 = fmaf(m, k.y, p1);
-        p2 = fmaf(m, k.z, p2);
-        p3 = fmaf(m, k.w, p3);
-      }
-      f0.add(p0);
-      f1.add(p1);
-      f2.add(p2);
-      f3.add(p3);
-    }
-    const int baseN = (a + RN) + HN * (b + RN) + HN2 * (c + RN);
-    for (int s = 0; s < st.n_near; ++s) {
-      int dx, dy, dz;
-      unpack(__ldg(st.near_ + s), dx, dy, dz);
-      const double m = halo64[baseN + dx + HN * dy + HN2 * dz];
-      const double2* kp = reinterpret_cast<const double2*>(st.kappa + kbase + dx + W * dy + W * W * dz);
-      const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
-      s0 = fma(m, ka.x, s0);
-      s1 = fma(m, ka.y, s1);
-      s2 = fma(m, kb.x, s2);
-      s3 = fma(m, kb.y, s3);
-    }
-    s0 += f0.value();
-    s1 += f1.value();
-    s2 += f2.value();
-    s3 += f3.value();
-  } else {
-    const double* halo = reinterpret_cast<const double*>(smem);
-    const int base = (a + R) + H * (b + R) + H2 * (c + R);
-    for (int pass = 0; pass < 2; ++pass) {
-      const int* tb = pass == 0 ? tab : st.near_;
-      const int nt = pass == 0 ? ntab : st.n_near;
-      for (int s = 0; s < nt; ++s) {
-        int dx, dy, dz;
-        unpack(__ldg(tb + s), dx, dy, dz);
-        const double m = halo[base + dx + H * dy + H2 * dz];
-        const double2* kp = reinterpret_cast<const double2*>(st.kappa + kbase + dx + W * dy + W * W * dz);
-        const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
-        s0 = fma(m, ka.x, s0);
-        s1 = fma(m, ka.y, s1);
-        s2 = fma(m, kb.x, s2);
-        s3 = fma(m, kb.y, s3);
-      }
-    }
-  }
+  const int n_far = lvl == 0 ? st.n_root : st.n_st;
   const double ih = 1.0 / t.h[lvl], ih2 = ih * ih;
-  double L0 = s0 * ih, L1[3] = {s1 * ih2, s2 * ih2, s3 * ih2}, dg[3] = {0.0, 0.0, 0.0};
-  if (refined_nbr) {  // block-uniform
-    // Boundary pairs with the threads re-assigned to the cells of this half in
+  double L0[2], L1[2][3];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    int p, zh, a, b, c;
+    cell_of(half, threadIdx.x, p, zh, a, b, c);
+    const int2* __restrict__ far = (lvl == 0 ? st.leaf_root : st.leaf_far) + p * n_far;
+    const int2* __restrict__ nr = st.leaf_near + p * st.n_near;
+    const int lane_f = (a >> 1) + gf.PY * (b >> 1) + gf.PZ * (c >> 1);
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // float64 sums, unit cell width
+    if (MIXED) {
+      const int lane_n = (a >> 1) + gn.PY * (b >> 1) + gn.PZ * (c >> 1);
+      const int n_blocks = (n_far + kAccBlock - 1) / kAccBlock;
+      const int near_per = n_blocks > 0 ? (st.n_near + n_blocks - 1) / n_blocks : st.n_near;
+      KF f0, f1, f2, f3;
+      f0 = 0.0f, f1 = 0.0f, f2 = 0.0f, f3 = 0.0f;
+      int sn = 0;
+      for (int s0i = 0; s0i < n_far || sn < st.n_near; s0i += kAccBlock) {
+        const int s1i = min(s0i + kAccBlock, n_far);
+        float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
+        for (int s = s0i; s < s1i; ++s) {
+          const int2 e = __ldg(far + s);
+          const float m = halo32[lane_f + e.x];
+          const float4 k = __ldg(st.kappa32 + e.y);
+          p0 = fmaf(m, k.x, p0);
+          p1 = fmaf(m, k.y, p1);
+          p2 = fmaf(m, k.z, p2);
+          p3 = fmaf(m, k.w, p3);
+        }
+        f0.add(p0);
+        f1.add(p1);
+        f2.add(p2);
+        f3.add(p3);
+        const int sn1 = min(sn + near_per, st.n_near);
+        for (; sn < sn1; ++sn) {
+          const int2 e = __ldg(nr + sn);
+          const double m = halo64[lane_n + e.x];
+          const double2* kp = reinterpret_cast<const double2*>(st.kappa + e.y);
+          const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
+          s0 = fma(m, ka.x, s0);
+          s1 = fma(m, ka.y, s1);
+          s2 = fma(m, kb.x, s2);
+          s3 = fma(m, kb.y, s3);
+        }
+      }
+      s0 += f0.value();
+      s1 += f1.value();
+      s2 += f2.value();
+      s3 += f3.value();
+    } else {
+      for (int pass = 0; pass < 2; ++pass) {
+        const int2* __restrict__ tb = pass == 0 ? far : nr;
+        const int nt = pass == 0 ? n_far : st.n_near;
+        for (int s = 0; s < nt; ++s) {
+          const int2 e = __ldg(tb + s);
+          const double m = halo64[lane_f + e.x];
+          const double2* kp = reinterpret_cast<const double2*>(st.kappa + e.y);
+          const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
+          s0 = fma(m, ka.x, s0);
+          s1 = fma(m, ka.y, s1);
+          s2 = fma(m, kb.x, s2);
+          s3 = fma(m, kb.y, s3);
+        }
+      }
+    }
+    L0[half] = s0 * ih;
+    L1[half][0] = s1 * ih2;
+    L1[half][1] = s2 * ih2;
+    L1[half][2] = s3 * ih2;
+  }
+  double dg[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  if (any_refined) {  // block-uniform
+    // Boundary pairs with the threads re-assigned to the cells of each half in
     // decreasing order of load (balanced warps); the results go back to the owning
     // threads through shared memory (the halo is no longer needed).
     __syncthreads();
     double* res = reinterpret_cast<double*>(smem);  // [512][7]
-    const int lb = st.bnd_perm[(int64_t)st.bnd_index[node] * 512 + half * 256 + threadIdx.x];
-    double v[7];
-    if constexpr (MIXED) {
-      Acc<KF> acc;
-      acc_zero(acc);
-      boundary_pairs<true>(t, node, lb, st, mp, mp32, acc);
-      v[0] = acc.L0.value() * ih;
-      for (int i = 0; i < 3; ++i) v[1 + i] = acc.L1[i].value() * ih2, v[4 + i] = acc.dg[i].value() * ih2;
-    } else {
-      Acc<double> acc;
-      acc_zero(acc);
-      boundary_pairs<false>(t, node, lb, st, mp, mp32, acc);
-      v[0] = acc.L0;
-      for (int i = 0; i < 3; ++i) v[1 + i] = acc.L1[i], v[4 + i] = acc.dg[i];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int lb = st.bnd_perm[(int64_t)st.bnd_index[node] * 512 + half * 256 + threadIdx.x];
+      double v[7];
+      if constexpr (MIXED) {
+        Acc<KF> acc;
+        acc_zero(acc);
+        boundary_pairs<true>(t, node, lb, st, mp, mp32, acc);
+        v[0] = acc.L0.value() * ih;
+        for (int i = 0; i < 3; ++i) v[1 + i] = acc.L1[i].value() * ih2, v[4 + i] = acc.dg[i].value() * ih2;
+      } else {
+        Acc<double> acc;
+        acc_zero(acc);
+        boundary_pairs<false>(t, node, lb, st, mp, mp32, acc);
+        v[0] = acc.L0;
+        for (int i = 0; i < 3; ++i) v[1 + i] = acc.L1[i], v[4 + i] = acc.dg[i];
+      }
+      for (int i = 0; i < 7; ++i) res[lb * 7 + i] = v[i];
     }
-    for (int i = 0; i < 7; ++i) res[lb * 7 + i] = v[i];
     __syncthreads();
-    const int l = a + 8 * b + 64 * c;
-    L0 += res[l * 7];
-    for (int i = 0; i < 3; ++i) L1[i] += res[l * 7 + 1 + i], dg[i] = res[l * 7 + 4 + i];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      int p, zh, a, b, c;
+      cell_of(half, threadIdx.x, p, zh, a, b, c);
+      const int l = a + 8 * b + 64 * c;
+      L0[half] += res[l * 7];
+      for (int i = 0; i < 3; ++i) L1[half][i] += res[l * 7 + 1 + i], dg[half][i] = res[l * 7 + 4 + i];
+    }
   }
   const int64_t NC = t.NC;
-  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
-  loc[G_L0 * NC + tgt] = L0;
-  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = L1[i], loc[(G_DG + i) * NC + tgt] = dg[i];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    int p, zh, a, b, c;
+    cell_of(half, threadIdx.x, p, zh, a, b, c);
+    const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
+    loc[G_L0 * NC + tgt] = L0[half];
+    for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = L1[half][i], loc[(G_DG + i) * NC + tgt] = dg[half][i];
+  }
 }
 
 }  // namespace items

@@ -29,7 +29,16 @@ struct Stencils {
   const int* cell_ent_off;
   const unsigned short* bnd_perm;  // per boundary leaf node: cells of each half by decreasing load
   const int* bnd_index;            // per node: row of bnd_perm or -1
+  // Leaf items, per parity class p of the target cell and stencil entry s:
+  // {offset into the shared-memory mass halo, row of kappa / kappa32} (see items.cuh).
+  const int2* leaf_far;   // [8][n_st]   parity stencil (far halo)
+  const int2* leaf_root;  // [8][n_root] level-0 stencil (far halo)
+  const int2* leaf_near;  // [8][n_near] near offsets (mixed: near float64 halo; float64: far halo)
 };
+
+// Host: the leaf-item tables above for the given stencils and precision mode.
+void build_leaf_tables(const int* parity, int n_st, const int* root, int n_root, const int* near_, int n_near, int R,
+                       int RN, bool mixed, int2* far_out, int2* root_out, int2* near_out);
 
 struct CrossList {
   const int64_t* targets;

@@ -21,10 +21,9 @@ __global__ void __launch_bounds__(items::kThreads, MIXED ? 3 : 1) k_interior_ite
                                                                      Stencils st, const double* __restrict__ mp,
                                                                      const float* __restrict__ mp32,
                                                                      double* __restrict__ loc) {
-  extern __shared__ __align__(16) unsigned char smem[];
   const int node = nodes[blockIdx.x >> 1];
   if (MIXED)
-    items::interior_f32(t, node, blockIdx.x & 1, st, mp32, loc, smem);
+    items::interior_f32(t, node, blockIdx.x & 1, st, mp32, loc);
   else
     items::interior_f64(t, node, blockIdx.x & 1, st, mp, loc);
 }
@@ -35,10 +34,11 @@ __global__ void __launch_bounds__(items::kThreads) k_leaf_items(DevTree t, const
                                                                  const float* __restrict__ mp32,
                                                                  double* __restrict__ loc) {
   extern __shared__ __align__(16) unsigned char smem[];
-  items::leaf_item<MIXED>(t, nodes[blockIdx.x >> 1], blockIdx.x & 1, st, mp, mp32, loc, smem);
+  items::leaf_item<MIXED>(t, nodes[blockIdx.x], st, mp, mp32, loc, smem);
 }
 
-// item = (node << 2) | (kind << 1) | half, kind 0 = interior, 1 = leaf
+// item = (node << 2) | (kind << 1) | half, kind 0 = interior (one half of the node),
+// 1 = leaf (the whole node; half unused)
 template <bool MIXED, int MINB>
 __global__ void __launch_bounds__(items::kThreads, MINB)
     k_persistent(DevTree t, const int* __restrict__ queue, int n_items, int* __restrict__ counter, Stencils st,
@@ -54,10 +54,10 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
     const int it = queue[k];
     const int node = it >> 2, half = it & 1;
     if ((it >> 1) & 1) {
-      items::leaf_item<MIXED>(t, node, half, st, mp, mp32, loc, smem);
+      items::leaf_item<MIXED>(t, node, st, mp, mp32, loc, smem);
     } else {
       if (MIXED)
-        items::interior_f32(t, node, half, st, mp32, loc, smem);
+        items::interior_f32(t, node, half, st, mp32, loc);
       else
         items::interior_f64(t, node, half, st, mp, loc);
     }
@@ -66,11 +66,8 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
 
 // Resident blocks per SM of a persistent variant (sets its shared-memory limit);
 // called once per handle, outside any stream capture.
-// Dynamic shared memory of the persistent kernel: the larger of the two items' needs.
-size_t persistent_smem_bytes(const Stencils& st, bool mixed) {
-  const size_t leaf = items::leaf_smem_bytes(st, mixed);
-  return mixed ? std::max(leaf, items::interior_smem_bytes()) : leaf;
-}
+// Dynamic shared memory of the persistent kernel (the interior items use none).
+size_t persistent_smem_bytes(const Stencils& st, bool mixed) { return items::leaf_smem_bytes(st, mixed); }
 
 template <bool MIXED, int MINB>
 cudaError_t persistent_occupancy(const Stencils& st, int* per_sm) {
@@ -95,22 +92,35 @@ cudaError_t persistent_launch(const DevTree& t, const InteractArgs& a, cudaStrea
 
 }  // namespace
 
+void build_leaf_tables(const int* parity, int n_st, const int* root, int n_root, const int* near_, int n_near, int R,
+                       int RN, bool mixed, int2* far_out, int2* root_out, int2* near_out) {
+  const items::HaloGeom gf = items::far_geom(R), gn = mixed ? items::near_geom(RN) : items::far_geom(R);
+  const int W = 2 * R + 1, kbase = R + W * R + W * W * R;
+  // entry of offset d for targets of parity (pa, pb, pc) in a halo of border g.r
+  auto entry = [&](const items::HaloGeom& g, int pa, int pb, int pc, int e) {
+    const int dx = (int)(int8_t)(e & 0xff), dy = (int)(int8_t)((e >> 8) & 0xff), dz = (int)(int8_t)((e >> 16) & 0xff);
+    return make_int2(items::halo_index(g, pa + g.r + dx, pb + g.r + dy, pc + g.r + dz), kbase + dx + W * dy + W * W * dz);
+  };
+  for (int p = 0; p < 8; ++p) {
+    const int pa = p & 1, pb = (p >> 1) & 1, pc = p >> 2;
+    for (int s = 0; s < n_st; ++s) far_out[p * n_st + s] = entry(gf, pa, pb, pc, parity[p * n_st + s]);
+    for (int s = 0; s < n_root; ++s) root_out[p * n_root + s] = entry(gf, pa, pb, pc, root[s]);
+    for (int s = 0; s < n_near; ++s) near_out[p * n_near + s] = entry(gn, pa, pb, pc, near_[s]);
+  }
+}
+
 cudaError_t configure_interact_kernels() {
   cudaError_t e = cudaSuccess;
   const int big = 200 * 1024;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leaf_items<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leaf_items<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_interior_items<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)items::interior_smem_bytes());
   return e;
 }
 
 cudaError_t launch_interior_items(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
   if (a.n_interior == 0) return cudaSuccess;
   if (a.mixed)
-    k_interior_items<true><<<2 * a.n_interior, items::kThreads, items::interior_smem_bytes(), s>>>(
-        t, a.interior, a.st, a.mp, a.mp32, a.loc);
+    k_interior_items<true><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp, a.mp32, a.loc);
   else
     k_interior_items<false><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp, a.mp32, a.loc);
   return cudaGetLastError();
@@ -120,9 +130,9 @@ cudaError_t launch_leaf_items(const DevTree& t, const InteractArgs& a, cudaStrea
   if (a.n_leaf == 0) return cudaSuccess;
   const size_t smem = items::leaf_smem_bytes(a.st, a.mixed);
   if (a.mixed)
-    k_leaf_items<true><<<2 * a.n_leaf, items::kThreads, smem, s>>>(t, a.leaf, a.st, a.mp, a.mp32, a.loc);
+    k_leaf_items<true><<<a.n_leaf, items::kThreads, smem, s>>>(t, a.leaf, a.st, a.mp, a.mp32, a.loc);
   else
-    k_leaf_items<false><<<2 * a.n_leaf, items::kThreads, smem, s>>>(t, a.leaf, a.st, a.mp, a.mp32, a.loc);
+    k_leaf_items<false><<<a.n_leaf, items::kThreads, smem, s>>>(t, a.leaf, a.st, a.mp, a.mp32, a.loc);
   return cudaGetLastError();
 }
 
