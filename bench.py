@@ -234,6 +234,30 @@ def roofline_of(info, mean_stage_ms, peaks):
             "frac": achieved / peak, "traffic": None, "peak_source": "measured" if peaks else "fallback"}
 
 
+def stage_rates(info, mean_stage_ms, peaks):
+    """Per stage: time, and either the float32 / float64 flop rates as fractions of
+    their peaks (interaction stages) or HBM GB/s as a fraction of the measured copy
+    bandwidth (tree passes; algorithmic bytes, every value read or written once)."""
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {}
+    for i, st in enumerate(info):
+        ms = float(mean_stage_ms[i])
+        if ms <= 0:
+            continue
+        d = {"ms": round(ms, 4)}
+        if st["flops"] > 0:
+            f64 = st["flops64"]
+            f32 = st["flops"] - f64
+            d["fp32_frac"] = round(f32 / (ms / 1e3) / 1e12 / PEAK_FP32_TFLOPS, 4)
+            d["fp64_frac"] = round(f64 / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS, 4)
+        elif st["bytes"] > 0:
+            gbs = st["bytes"] / (ms / 1e3) / 1e9
+            d["gbs"] = round(gbs, 1)
+            d["hbm_frac"] = round(gbs / hbm, 4)
+        out[st["name"]] = d
+    return out
+
+
 def interaction_fp64_frac(info, mean_stage_ms):
     """float64 flop rate of all interaction stages together (their float64 flops over
     their summed event time) as a fraction of the float64 peak."""
@@ -303,7 +327,8 @@ def run_ours(args):
     gopt = lambda k: binding.octo_fmm_get_option(fmm.handle, k)  # noqa: E731
     strategy = {"chosen": {1: "per-kind launches", 2: "persistent work queue"}[gopt(3)],
                 "register_budget_blocks_per_sm": gopt(4),
-                "autotune_us": {"per_kind": gopt(10), "persistent_1": gopt(11), "persistent_2": gopt(12)}}
+                "autotune_us": {"per_kind": gopt(10), "persistent_1": gopt(11), "persistent_2": gopt(12),
+                                "persistent_3": gopt(13)}}
 
     if precision == binding.OCTO_MIXED and not args.no_fp64:
         del fmm
@@ -333,6 +358,7 @@ def run_ours(args):
         "roofline": roof,
         "interaction_strategy": strategy,
         "stages_ms": {info[i]["name"]: round(float(mean_stage[i]), 4) for i in range(len(info))},
+        "stage_rates": stage_rates(info, mean_stage, _measured_peaks()),
         "e2e": e2e,
         "gpu_launches": int(launches * args.steps),
         "clocks": clocks,

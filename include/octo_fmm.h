@@ -138,23 +138,27 @@ int octo_fmm_read_state(octo_fmm_t h, int which, double* host_out);
  *         forces call (default; times the candidates on this tree and keeps the
  *         fastest), 1 = one launch per item kind over all levels, 2 = one
  *         persistent launch pulling interior and leaf items of every level from a
- *         work queue;
- *  key 4: register budget of the persistent launch: 1 or 2 resident blocks per SM.
+ *         work queue (in mixed precision the float64 near field of the leaf nodes
+ *         is a separate item kind, interleaved with the float32 items so that
+ *         both pipes of every SM work at once);
+ *  key 4: register budget of the persistent launch: 1 or 2 resident blocks per SM,
+ *         or 3 (mixed precision only).
  * Setting an option drops the captured graph.  Returns OCTO_EINVAL for an unknown
  * key or value. */
 int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value);
 
 /* Reads an option (keys 1-4 above; key 3 reports the strategy in use after
- * autotuning) or an autotuner measurement: keys 10, 11, 12 = mean interaction
- * time in microseconds of per-kind launches, persistent (1 block/SM budget) and
- * persistent (2 blocks/SM budget); 0 before autotuning. */
+ * autotuning) or an autotuner measurement: keys 10, 11, 12, 13 = mean interaction
+ * time in microseconds of per-kind launches and of the persistent launch with the
+ * 1, 2 and 3 blocks/SM budgets; 0 when not measured (before autotuning, and key 13
+ * in float64 mode). */
 int octo_fmm_get_option(octo_fmm_t h, int key, int64_t* value);
 
 /* Number of kernel launches one octo_fmm_forces call enqueues. */
 int octo_fmm_launches_per_solve(octo_fmm_t h);
 
 /* Stage introspection for measurement.  The solve is a fixed list of stages, one
- * kernel launch each (e.g. "p2m", "m2m_l3", "m2l_interior", "leaf_conv",
+ * kernel launch each (e.g. "p2m", "m2m_l3", "m2l_interior", "leaf", "cross_cells",
  * "l2l_l2").  octo_fmm_stage_count returns their number; octo_fmm_stage_info gives
  * stage i's name (owned by the handle), the interactions it processes (pairs), the
  * cells it writes, its algorithmic floating-point operations (the per-pair

@@ -104,12 +104,12 @@ struct octo_fmm {
   // batched interaction phase: strategy (MODE_*), persistent work queue and counter
   int mode = 0, requested_mode = 0;
   int min_blocks = 1, n_sm = 0;
-  int persist_per_sm[3] = {0, 0, 0};  // resident blocks per SM of the persistent variants (index = budget)
+  int persist_per_sm[4] = {0, 0, 0, 0};  // resident blocks per SM of the persistent variants (index = budget)
   int* d_queue = nullptr;
   int n_items = 0;
   int* d_counter = nullptr;
   int* d_err = nullptr;  // device-side check word of the adjoint kernels
-  float tune_ms[3] = {0, 0, 0};  // measured interaction time per strategy (autotune)
+  float tune_ms[4] = {0, 0, 0, 0};  // measured interaction time per strategy candidate (autotune)
   double *d_mpb = nullptr, *d_locb = nullptr;  // adjoint workspace
   int* d_general = nullptr;
   int n_general = 0;
@@ -120,6 +120,7 @@ struct octo_fmm {
   // state
   double *d_mp = nullptr, *d_loc = nullptr;
   float* d_mp32 = nullptr;    // float32 multipoles (mixed precision only)
+  double* d_near = nullptr;   // [4][leaf cells] near-field sums (mixed precision only)
   float4* d_kappa32 = nullptr;
   DevTree dt;
   Stencils st;
@@ -168,7 +169,7 @@ void free_all(octo_fmm* h) {
   void* ptrs[] = {h->d_level,    h->d_parent,  h->d_octant, h->d_children, h->d_nbr,    h->d_leaf_id,
                   h->d_ijk,      h->d_interior, h->d_leaf,  h->d_boundary, h->d_st_parity, h->d_st_root,
                   h->d_st_near,  h->d_kappa,   h->d_xc_t,   h->d_xc_off,   h->d_xc_ent,  h->d_xc_tab,  h->d_xc_counter,
-                  h->d_mp,       h->d_loc,      h->d_io,        h->d_mp32,
+                  h->d_mp,       h->d_loc,      h->d_io,        h->d_mp32,     h->d_near,
                   h->d_cell_ent, h->d_cell_ent_off, h->d_bnd_perm,
                   h->d_bnd_index, h->d_mpb,    h->d_locb,
                   h->d_general,  h->d_queue,   h->d_counter, h->d_err,
@@ -187,7 +188,7 @@ void free_all(octo_fmm* h) {
 }
 
 // Kinds in solve order; [S_M2L, S_CROSS_LEAF] is the interaction phase.
-enum StageKind { S_P2M, S_M2M, S_M2L, S_CONV, S_PERSIST, S_CROSS_CELLS, S_CROSS_FULL, S_CROSS_LEAF, S_L2L };
+enum StageKind { S_P2M, S_M2M, S_M2L, S_CONV, S_NEAR, S_PERSIST, S_CROSS_CELLS, S_CROSS_FULL, S_CROSS_LEAF, S_L2L };
 
 // Interaction strategies (option key 3).
 enum { MODE_AUTO = 0, MODE_PER_KIND = 1, MODE_PERSISTENT = 2 };
@@ -244,10 +245,11 @@ void make_stages(octo_fmm* h) {
       case S_P2M: bytes = cells * 16; break;                      // rho in, m out
       case S_M2M: bytes = cells * (8 * 20 + 20) * 8; break;        // 8 children in, parent out
       case S_M2L: far = pairs * f_int; break;
-      case S_CONV:
+      case S_CONV:  // mixed precision: the near field is the separate S_NEAR stage
         far = P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
-        near = P.kernel_pairs[2] * kConvFlopsPerPair;
+        if (h->precision != OCTO_MIXED) near = P.kernel_pairs[2] * kConvFlopsPerPair;
         break;
+      case S_NEAR: near = P.kernel_pairs[2] * kConvFlopsPerPair; break;
       case S_PERSIST:
         far = P.kernel_pairs[0] * f_int + P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
         near = P.kernel_pairs[2] * kConvFlopsPerPair;
@@ -283,9 +285,15 @@ void make_stages(octo_fmm* h) {
     if (!P.interior_nodes.empty())
       add(S_M2L, 0, 0, mixed ? "m2l_interior_f32" : "m2l_interior", P.kernel_pairs[0],
           (int64_t)P.interior_nodes.size() * kCells);
-    if (!P.leaf_nodes.empty())
-      add(S_CONV, 0, 0, mixed ? "leaf_mixed" : "leaf", P.kernel_pairs[1] + P.kernel_pairs[2] + P.kernel_pairs[3],
-          (int64_t)P.leaf_nodes.size() * kCells);
+    if (!P.leaf_nodes.empty()) {
+      if (mixed) {
+        add(S_CONV, 0, 0, "leaf_far_f32", P.kernel_pairs[1] + P.kernel_pairs[3], (int64_t)P.leaf_nodes.size() * kCells);
+        add(S_NEAR, 0, 0, "leaf_near_f64", P.kernel_pairs[2], (int64_t)P.leaf_nodes.size() * kCells);
+      } else {
+        add(S_CONV, 0, 0, "leaf", P.kernel_pairs[1] + P.kernel_pairs[2] + P.kernel_pairs[3],
+            (int64_t)P.leaf_nodes.size() * kCells);
+      }
+    }
   }
   if (h->xc.n_slices > 0) {
     int64_t nt = 0;
@@ -329,6 +337,8 @@ InteractArgs interact_args(const octo_fmm* h) {
   a.n_interior = (int)P.interior_nodes.size();
   a.leaf = h->d_leaf;
   a.n_leaf = (int)P.leaf_nodes.size();
+  a.nearf = h->d_near;
+  a.NL = h->n_leaf_cells();
   a.queue = h->d_queue;
   a.n_items = h->n_items;
   a.counter = h->d_counter;
@@ -345,13 +355,14 @@ cudaError_t enq_stage(octo_fmm* h, const octo_fmm::Stage& st, const double* rho,
     case S_M2M: return launch_m2m(h->dt, st.a, st.b, h->d_mp, h->d_mp32, s);
     case S_M2L: return launch_interior_items(h->dt, interact_args(h), s);
     case S_CONV: return launch_leaf_items(h->dt, interact_args(h), s);
+    case S_NEAR: return launch_near_items(h->dt, interact_args(h), s);
     case S_PERSIST: return launch_persistent(h->dt, interact_args(h), s);
     case S_CROSS_CELLS: return launch_cross_cells(h->dt, h->xc, h->d_mp, h->d_loc, h->xc_grid, s);
     case S_CROSS_FULL:
       return launch_cross_list(h->dt, h->xg.f, true, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
     case S_CROSS_LEAF:
       return launch_cross_list(h->dt, h->xg.l, false, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
-    case S_L2L: return launch_l2l(h->dt, st.a, st.b, h->d_mp, h->d_loc, phi, g, h->n_leaf_cells(), s);
+    case S_L2L: return launch_l2l(h->dt, st.a, st.b, h->d_mp, h->d_loc, phi, g, h->n_leaf_cells(), h->d_near, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -433,9 +444,10 @@ int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
   if (e == cudaSuccess) e = enq_upward(h, rho, ts);
   struct Cand {
     int mode, minb;
-  } cands[3] = {{MODE_PER_KIND, 1}, {MODE_PERSISTENT, 1}, {MODE_PERSISTENT, 2}};
+  } cands[4] = {{MODE_PER_KIND, 1}, {MODE_PERSISTENT, 1}, {MODE_PERSISTENT, 2}, {MODE_PERSISTENT, 3}};
+  const int n_cands = h->precision == OCTO_MIXED ? 4 : 3;  // budget 3: mixed precision only
   int best = 0;
-  for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+  for (int c = 0; c < n_cands && e == cudaSuccess; ++c) {
     h->mode = cands[c].mode;
     h->min_blocks = cands[c].minb;
     e = rebuild_stages(h);
@@ -540,6 +552,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   if (e == cudaSuccess) e = cudaMalloc(&h->d_mp, sizeof(double) * N_MP * NC);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_loc, sizeof(double) * N_LOC * NC);
   if (e == cudaSuccess && precision == OCTO_MIXED) e = cudaMalloc(&h->d_mp32, sizeof(float) * N_MP * NC);
+  if (e == cudaSuccess && precision == OCTO_MIXED) e = cudaMalloc(&h->d_near, sizeof(double) * 4 * h->n_leaf_cells());
   if (e == cudaSuccess) e = cudaMalloc(&h->d_io, sizeof(double) * 5 * h->n_leaf_cells());
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_stage, sizeof(double) * 5 * h->n_leaf_cells());
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
@@ -597,38 +610,57 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     delete h;
     return create_fail(OCTO_ECUDA, m);
   }
-  // persistent work queue.  Interior items of the root first (the largest), then of
-  // the other levels; leaf items with refined neighbours before the other leaf items.
-  // Float64: all interior items, then all leaf items.  Mixed precision: the two lists
-  // merged in proportion (each prefix of the queue holds the same fraction of both),
-  // so that float32-bound interior items and float64-bound leaf items (their
-  // near field) run side by side on every SM and use both pipes.
+  // persistent work queue (item = (node << 3) | (kind << 1) | half).  Interior items
+  // (kind 0, one per half) of the root first (the largest), then of the other
+  // levels; leaf items (kind 1, whole node) with refined neighbours before the
+  // others.  Float64: all interior items, then all leaf items.  Mixed precision:
+  // the float32-bound items (interior, leaf far field) and the float64-bound near
+  // items (kind 2) are merged so that every prefix of the queue holds the same
+  // fraction of the estimated work of both (SM cycles: an M2L pair ~240 float32
+  // instructions at 128 per cycle, a far pair ~7, a near pair 4 DFMA at 2 per
+  // cycle), so that the two pipes of every SM stay busy side by side.
   {
-    std::vector<int32_t> qi, ql, q;
-    auto push = [](std::vector<int32_t>& v, int node, int kind) {  // interior: two halves; leaf: whole node
-      v.push_back((node << 2) | (kind << 1) | 0);
-      if (kind == 0) v.push_back((node << 2) | (kind << 1) | 1);
-    };
-    for (int k : P.interior_nodes)
-      if (P.level[k] == 0) push(qi, k, 0);
-    for (int k : P.interior_nodes)
-      if (P.level[k] != 0) push(qi, k, 0);
+    std::vector<int32_t> q32, q64, q;
+    std::vector<double> w32, w64;
+    const double n_far = (double)P.n_st, n_near = (double)P.st_near.size();
+    auto item = [](int node, int kind, int half) { return (node << 3) | (kind << 1) | half; };
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k : P.interior_nodes)
+        if ((P.level[k] == 0) == (pass == 0))
+          for (int half = 0; half < 2; ++half) {
+            q32.push_back(item(k, 0, half));
+            w32.push_back(256.0 * (P.level[k] == 0 ? (double)P.st_root.size() : n_far) * 240.0 / 128.0);
+          }
     std::vector<char> bnd(P.n_nodes, 0);
     for (int k : P.boundary_nodes) bnd[k] = 1;
-    for (int k : P.leaf_nodes)
-      if (bnd[k]) push(ql, k, 1);
-    for (int k : P.leaf_nodes)
-      if (!bnd[k]) push(ql, k, 1);
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k : P.leaf_nodes)
+        if ((bnd[k] != 0) == (pass == 0)) {
+          q32.push_back(item(k, 1, 0));
+          w32.push_back(512.0 * n_far * 7.0 / 128.0);
+          if (precision == OCTO_MIXED) {
+            q64.push_back(item(k, 2, 0));
+            w64.push_back(512.0 * n_near * 4.0 / 2.0);
+          }
+        }
     if (precision == OCTO_MIXED) {
-      size_t i = 0, l = 0;
-      while (i < qi.size() || l < ql.size()) {
-        // take an interior item while its list is not ahead: i / |qi| <= l / |ql|
-        const bool take_i = l == ql.size() || (i < qi.size() && i * ql.size() <= l * qi.size());
-        q.push_back(take_i ? qi[i++] : ql[l++]);
+      double t32 = 0, t64 = 0, c32 = 0, c64 = 0;
+      for (double v : w32) t32 += v;
+      for (double v : w64) t64 += v;
+      size_t i = 0, j = 0;
+      while (i < q32.size() || j < q64.size()) {
+        // take the list whose consumed fraction of its total work is smaller
+        const bool take32 = j == q64.size() || (i < q32.size() && c32 * t64 <= c64 * t32);
+        if (take32) {
+          c32 += w32[i];
+          q.push_back(q32[i++]);
+        } else {
+          c64 += w64[j];
+          q.push_back(q64[j++]);
+        }
       }
     } else {
-      q = qi;
-      q.insert(q.end(), ql.begin(), ql.end());
+      q = q32;
     }
     h->n_items = (int)q.size();
     e = upload(&h->d_queue, q);
@@ -637,7 +669,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = configure_interact_kernels();
-    for (int mb = 1; mb <= 2 && e == cudaSuccess; ++mb)
+    for (int mb = 1; mb <= (precision == OCTO_MIXED ? 3 : 2) && e == cudaSuccess; ++mb)
       e = persistent_blocks_per_sm(precision == OCTO_MIXED, mb, h->st, &h->persist_per_sm[mb]);
     int xc_per_sm = 0;
     if (e == cudaSuccess && h->xc.n_slices > 0) e = cross_cells_blocks_per_sm(h->xc, &xc_per_sm);
@@ -840,7 +872,7 @@ int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value) {
     cudaError_t e = rebuild_stages(h);
     return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "set strategy");
   }
-  if (key == 4 && (value == 1 || value == 2)) {
+  if (key == 4 && (value == 1 || value == 2 || (value == 3 && h->precision == OCTO_MIXED))) {
     h->min_blocks = (int)value;
     cudaError_t e = rebuild_stages(h);
     return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "set blocks");
@@ -893,7 +925,8 @@ int octo_fmm_get_option(octo_fmm_t h, int key, int64_t* value) {
     case 4: *value = h->min_blocks; return OCTO_OK;
     case 10:
     case 11:
-    case 12: *value = (int64_t)(1000.0f * h->tune_ms[key - 10]); return OCTO_OK;
+    case 12:
+    case 13: *value = (int64_t)(1000.0f * h->tune_ms[key - 10]); return OCTO_OK;
   }
   return fail(h, OCTO_EINVAL, "unknown option");
 }

@@ -210,13 +210,16 @@ __host__ __device__ inline int halo_index(const HaloGeom& g, int hx, int hy, int
 }
 
 // Shared memory of a leaf item: the far halo (float32 in the mixed path, float64
-// otherwise), the near float64 halo (mixed path), and at least 512 x 7 doubles
-// (the boundary results are exchanged through it).
+// otherwise), and at least 512 x 7 doubles (the boundary results are exchanged
+// through it).  The near item of the mixed path needs the near float64 halo.
 __host__ __device__ inline size_t leaf_smem_bytes(const Stencils& st, bool mixed) {
-  const HaloGeom gf = far_geom(st.radius), gn = near_geom(st.near_radius);
-  const size_t halo = mixed ? sizeof(float) * 8 * (size_t)gf.PQ + sizeof(double) * 8 * (size_t)gn.PQ
-                            : sizeof(double) * 8 * (size_t)gf.PQ;
+  const HaloGeom gf = far_geom(st.radius);
+  const size_t halo = (mixed ? sizeof(float) : sizeof(double)) * 8 * (size_t)gf.PQ;
   return halo > sizeof(double) * 512 * 7 ? halo : sizeof(double) * 512 * 7;
+}
+
+__host__ __device__ inline size_t near_smem_bytes(const Stencils& st) {
+  return sizeof(double) * 8 * (size_t)near_geom(st.near_radius).PQ;
 }
 
 // M2L from refined same-level neighbours into leaf cell l of a leaf node (leaf
@@ -271,23 +274,41 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
   }
 }
 
-// One leaf node per block (both halves): stage the halo once, then every thread
-// computes its cell of each half.  Mixed path: after every block of kAccBlock far
-// entries (float32) the thread takes its share of the near entries (float64), so
-// that each warp keeps both the float32 and the float64 pipe busy.
-template <bool MIXED>
-__device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Stencils& st,
-                                          const double* __restrict__ mp, const float* __restrict__ mp32,
-                                          double* __restrict__ loc, unsigned char* smem) {
-  const HaloGeom gf = far_geom(st.radius), gn = near_geom(st.near_radius);
-  const int R = gf.r, H = 2 * gf.G, RN = gn.r;
-  __shared__ int nleaf[27];  // leaf same-level neighbour (or the node itself), else -1
-  __shared__ int any_refined;
+// Stages the masses of the leaf same-level neighbourhood of `node` (cells within
+// border g.r of the node) into a parity-split halo; refined or missing neighbours
+// contribute zero.  nleaf: the 27 neighbours (or the node itself) if leaves, else -1.
+template <typename T>
+__device__ __forceinline__ void stage_halo(const HaloGeom& g, const int* nleaf, const double* __restrict__ mp,
+                                           T* halo) {
+  constexpr int kStage = 4;  // independent loads in flight per thread before their stores
+  const int H = 2 * g.G, R = g.r, n_halo = H * H * H;
+  for (int i0 = threadIdx.x; i0 < n_halo; i0 += kStage * blockDim.x) {
+    double m[kStage];
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int i = i0 + u * blockDim.x;
+      m[u] = 0.0;
+      if (i < n_halo) {
+        const int x = i % H - R, y = (i / H) % H - R, z = i / (H * H) - R;
+        const int sn = nleaf[((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1)];
+        if (sn >= 0) m[u] = __ldg(mp + (int64_t)sn * 512 + (x & 7) + 8 * (y & 7) + 64 * (z & 7));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n_halo) halo[halo_index(g, i % H, (i / H) % H, i / (H * H))] = (T)m[u];
+    }
+  }
+}
+
+// Leaf neighbour table of `node` into shared memory; returns whether any same-level
+// neighbour is refined (block-uniform).  Ends with a barrier.
+__device__ __forceinline__ bool load_leaf_neighbours(const DevTree& t, int node, int* nleaf, int* any_refined) {
   __syncthreads();  // the previous item may still read shared memory
   if (threadIdx.x < 27) {
     const int sn = t.nbr[27 * node + threadIdx.x];
-    const bool leaf = sn >= 0 && t.children[8 * sn] < 0;
-    nleaf[threadIdx.x] = leaf ? sn : -1;
+    nleaf[threadIdx.x] = sn >= 0 && t.children[8 * sn] < 0 ? sn : -1;
   }
   if (threadIdx.x == 0) {
     int any = 0;
@@ -295,25 +316,30 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
       const int sn = t.nbr[27 * node + o];
       any |= sn >= 0 && t.children[8 * sn] >= 0;
     }
-    any_refined = any;
+    *any_refined = any;
   }
   __syncthreads();
+  return *any_refined != 0;
+}
+
+// One leaf node per block (both halves): stage the halo once, then every thread
+// computes its cell of each half.  Mixed path: the float32 far field only (the
+// float64 near field is the separate near item, so that the two can run side by
+// side on an SM); float64 path: far and near field.
+template <bool MIXED>
+__device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Stencils& st,
+                                          const double* __restrict__ mp, const float* __restrict__ mp32,
+                                          double* __restrict__ loc, unsigned char* smem) {
+  const HaloGeom gf = far_geom(st.radius);
+  __shared__ int nleaf[27];
+  __shared__ int any_refined_s;
+  const bool any_refined = load_leaf_neighbours(t, node, nleaf, &any_refined_s);
   float* halo32 = reinterpret_cast<float*>(smem);
-  double* halo64 = MIXED ? reinterpret_cast<double*>(smem + sizeof(float) * 8 * (size_t)gf.PQ)
-                         : reinterpret_cast<double*>(smem);
-  for (int i = threadIdx.x; i < H * H * H; i += blockDim.x) {
-    const int hx = i % H, hy = (i / H) % H, hz = i / (H * H);
-    const int x = hx - R, y = hy - R, z = hz - R;
-    const int sn = nleaf[((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1)];
-    const double m = sn >= 0 ? mp[(int64_t)sn * 512 + (x & 7) + 8 * (y & 7) + 64 * (z & 7)] : 0.0;
-    if (MIXED) {
-      halo32[halo_index(gf, hx, hy, hz)] = (float)m;
-      if (x >= -RN && x < 8 + RN && y >= -RN && y < 8 + RN && z >= -RN && z < 8 + RN)
-        halo64[halo_index(gn, x + RN, y + RN, z + RN)] = m;
-    } else {
-      halo64[halo_index(gf, hx, hy, hz)] = m;
-    }
-  }
+  double* halo64 = reinterpret_cast<double*>(smem);
+  if (MIXED)
+    stage_halo(gf, nleaf, mp, halo32);
+  else
+    stage_halo(gf, nleaf, mp, halo64);
   __syncthreads();
   const int lvl = t.level[node];
   const int n_far = lvl == 0 ? st.n_root : st.n_st;
@@ -328,15 +354,12 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
     const int lane_f = (a >> 1) + gf.PY * (b >> 1) + gf.PZ * (c >> 1);
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // float64 sums, unit cell width
     if (MIXED) {
-      const int lane_n = (a >> 1) + gn.PY * (b >> 1) + gn.PZ * (c >> 1);
-      const int n_blocks = (n_far + kAccBlock - 1) / kAccBlock;
-      const int near_per = n_blocks > 0 ? (st.n_near + n_blocks - 1) / n_blocks : st.n_near;
       KF f0, f1, f2, f3;
       f0 = 0.0f, f1 = 0.0f, f2 = 0.0f, f3 = 0.0f;
-      int sn = 0;
-      for (int s0i = 0; s0i < n_far || sn < st.n_near; s0i += kAccBlock) {
+      for (int s0i = 0; s0i < n_far; s0i += kAccBlock) {
         const int s1i = min(s0i + kAccBlock, n_far);
         float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
+#pragma unroll 4
         for (int s = s0i; s < s1i; ++s) {
           const int2 e = __ldg(far + s);
           const float m = halo32[lane_f + e.x];
@@ -350,22 +373,11 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
         f1.add(p1);
         f2.add(p2);
         f3.add(p3);
-        const int sn1 = min(sn + near_per, st.n_near);
-        for (; sn < sn1; ++sn) {
-          const int2 e = __ldg(nr + sn);
-          const double m = halo64[lane_n + e.x];
-          const double2* kp = reinterpret_cast<const double2*>(st.kappa + e.y);
-          const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
-          s0 = fma(m, ka.x, s0);
-          s1 = fma(m, ka.y, s1);
-          s2 = fma(m, kb.x, s2);
-          s3 = fma(m, kb.y, s3);
-        }
       }
-      s0 += f0.value();
-      s1 += f1.value();
-      s2 += f2.value();
-      s3 += f3.value();
+      s0 = f0.value();
+      s1 = f1.value();
+      s2 = f2.value();
+      s3 = f3.value();
     } else {
       for (int pass = 0; pass < 2; ++pass) {
         const int2* __restrict__ tb = pass == 0 ? far : nr;
@@ -431,6 +443,50 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
     const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
     loc[G_L0 * NC + tgt] = L0[half];
     for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = L1[half][i], loc[(G_DG + i) * NC + tgt] = dg[half][i];
+  }
+}
+
+// Near item of the mixed path: the float64 near-field (P2P) sums of the 512 cells
+// of one leaf node, from a float64 halo of the near radius, into
+// nearf [4][NL] (leaf cell order; L0 and L1 in physical units), which L2P adds.
+// Its work is float64 fused multiply-adds only, so it fills the float64 pipe while
+// the float32 items of the same SM use the FMA pipe.
+__device__ __forceinline__ void near_item(const DevTree& t, int node, const Stencils& st,
+                                          const double* __restrict__ mp, double* __restrict__ nearf, int64_t NL,
+                                          unsigned char* smem) {
+  const HaloGeom gn = near_geom(st.near_radius);
+  __shared__ int nleaf_n[27];
+  __shared__ int any_refined_n;
+  load_leaf_neighbours(t, node, nleaf_n, &any_refined_n);
+  double* halo = reinterpret_cast<double*>(smem);
+  stage_halo(gn, nleaf_n, mp, halo);
+  __syncthreads();
+  const int lvl = t.level[node];
+  const double ih = 1.0 / t.h[lvl], ih2 = ih * ih;
+  const int64_t lid = t.leaf_id[node];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    int p, zh, a, b, c;
+    cell_of(half, threadIdx.x, p, zh, a, b, c);
+    const int2* __restrict__ nr = st.leaf_near + p * st.n_near;
+    const int lane = (a >> 1) + gn.PY * (b >> 1) + gn.PZ * (c >> 1);
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll 2
+    for (int s = 0; s < st.n_near; ++s) {
+      const int2 e = __ldg(nr + s);
+      const double m = halo[lane + e.x];
+      const double2* kp = reinterpret_cast<const double2*>(st.kappa + e.y);
+      const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
+      s0 = fma(m, ka.x, s0);
+      s1 = fma(m, ka.y, s1);
+      s2 = fma(m, kb.x, s2);
+      s3 = fma(m, kb.y, s3);
+    }
+    const int64_t k = lid * 512 + a + 8 * b + 64 * c;
+    nearf[k] = s0 * ih;
+    nearf[NL + k] = s1 * ih2;
+    nearf[2 * NL + k] = s2 * ih2;
+    nearf[3 * NL + k] = s3 * ih2;
   }
 }
 

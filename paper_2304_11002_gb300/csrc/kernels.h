@@ -67,8 +67,9 @@ cudaError_t launch_init_leaf(const DevTree& t, const int* leaf_nodes, int n_leaf
 cudaError_t launch_p2m(const DevTree& t, const int* leaf_nodes, int n_leaf_nodes, const double* rho, double* mp,
                        float* mp32, cudaStream_t s);
 cudaError_t launch_m2m(const DevTree& t, int node_begin, int node_end, double* mp, float* mp32, cudaStream_t s);
+// nearf (may be null): [4][n_leaf_cells] near-field L0, L1 of the leaf cells, added at L2P.
 cudaError_t launch_l2l(const DevTree& t, int node_begin, int node_end, const double* mp, double* loc, double* phi,
-                       double* g, int64_t n_leaf_cells, cudaStream_t s);
+                       double* g, int64_t n_leaf_cells, const double* nearf, cudaStream_t s);
 
 // ------------------------------------------------------------ same-level interactions (kernels_interact.cu)
 struct InteractArgs {
@@ -81,7 +82,9 @@ struct InteractArgs {
   int n_interior;
   const int* leaf;     // leaf nodes (all levels)
   int n_leaf;
-  const int* queue;    // persistent queue: (node << 2) | (kind << 1) | half, largest items first
+  double* nearf;       // mixed precision: [4][NL] near-field sums of the leaf cells (near items)
+  int64_t NL;          // leaf cells
+  const int* queue;    // persistent queue: (node << 3) | (kind << 1) | half, see kernels_interact.cu
   int n_items;
   int* counter;        // work counter of the persistent launch (device scratch)
   int grid;            // blocks of the persistent launch (SMs x resident blocks per SM)
@@ -94,6 +97,7 @@ cudaError_t configure_interact_kernels();
 cudaError_t persistent_blocks_per_sm(bool mixed, int min_blocks, const Stencils& st, int* per_sm);
 cudaError_t launch_interior_items(const DevTree& t, const InteractArgs& a, cudaStream_t s);
 cudaError_t launch_leaf_items(const DevTree& t, const InteractArgs& a, cudaStream_t s);
+cudaError_t launch_near_items(const DevTree& t, const InteractArgs& a, cudaStream_t s);  // mixed precision only
 cudaError_t launch_persistent(const DevTree& t, const InteractArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------ cross-level pairs (kernels_boundary.cu)

@@ -128,10 +128,11 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int node_begin, double* 
 // Child expansion += parent expansion shifted by delta = X_child - X_parent
 // (exact for the cubic Taylor polynomial), dg carried down unshifted.  At leaf
 // nodes the result is evaluated at the cell itself (L2P):
-//   phi = L0,  g = -L1 + dg.
+//   phi = L0,  g = -L1 + dg  (plus the near-field sums when they are kept apart).
 __global__ void __launch_bounds__(256) k_l2l(DevTree t, int node_begin, const double* __restrict__ mp,
                                              double* __restrict__ loc, double* __restrict__ phi,
-                                             double* __restrict__ g, int64_t NL) {
+                                             double* __restrict__ g, int64_t NL,
+                                             const double* __restrict__ nearf) {
   const int node = node_begin + (blockIdx.x >> 1);
   const int l = ((blockIdx.x & 1) << 8) + threadIdx.x;
   const int64_t NC = t.NC;
@@ -190,6 +191,10 @@ __global__ void __launch_bounds__(256) k_l2l(DevTree t, int node_begin, const do
   }
   if (leaf) {
     const int64_t k = (int64_t)t.leaf_id[node] * 512 + l;
+    if (nearf) {  // near-field sums kept apart by the mixed-precision interaction phase
+      L0 += nearf[k];
+      for (int i = 0; i < 3; ++i) L1[i] += nearf[(1 + i) * NL + k];
+    }
     phi[k] = L0;
     for (int i = 0; i < 3; ++i) g[i * NL + k] = -L1[i] + dg[i];
   } else {
@@ -224,9 +229,9 @@ cudaError_t launch_m2m(const DevTree& t, int b, int e, double* mp, float* mp32, 
 }
 
 cudaError_t launch_l2l(const DevTree& t, int b, int e, const double* mp, double* loc, double* phi, double* g,
-                       int64_t NL, cudaStream_t s) {
+                       int64_t NL, const double* nearf, cudaStream_t s) {
   if (e <= b) return cudaSuccess;
-  k_l2l<<<2 * (e - b), 256, 0, s>>>(t, b, mp, loc, phi, g, NL);
+  k_l2l<<<2 * (e - b), 256, 0, s>>>(t, b, mp, loc, phi, g, NL, nearf);
   return cudaGetLastError();
 }
 

@@ -37,12 +37,20 @@ __global__ void __launch_bounds__(items::kThreads) k_leaf_items(DevTree t, const
   items::leaf_item<MIXED>(t, nodes[blockIdx.x], st, mp, mp32, loc, smem);
 }
 
-// item = (node << 2) | (kind << 1) | half, kind 0 = interior (one half of the node),
-// 1 = leaf (the whole node; half unused)
+__global__ void __launch_bounds__(items::kThreads) k_near_items(DevTree t, const int* __restrict__ nodes, Stencils st,
+                                                                 const double* __restrict__ mp,
+                                                                 double* __restrict__ nearf, int64_t NL) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  items::near_item(t, nodes[blockIdx.x], st, mp, nearf, NL, smem);
+}
+
+// item = (node << 3) | (kind << 1) | half; kind 0 = interior (one half of the node),
+// 1 = leaf (the whole node), 2 = near field of a leaf node (mixed precision only)
 template <bool MIXED, int MINB>
 __global__ void __launch_bounds__(items::kThreads, MINB)
     k_persistent(DevTree t, const int* __restrict__ queue, int n_items, int* __restrict__ counter, Stencils st,
-                 const double* __restrict__ mp, const float* __restrict__ mp32, double* __restrict__ loc) {
+                 const double* __restrict__ mp, const float* __restrict__ mp32, double* __restrict__ loc,
+                 double* __restrict__ nearf, int64_t NL) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next;
   for (;;) {
@@ -52,8 +60,10 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
     const int k = next;
     if (k >= n_items) return;
     const int it = queue[k];
-    const int node = it >> 2, half = it & 1;
-    if ((it >> 1) & 1) {
+    const int node = it >> 3, half = it & 1, kind = (it >> 1) & 3;
+    if (kind == 2) {
+      if (MIXED) items::near_item(t, node, st, mp, nearf, NL, smem);
+    } else if (kind == 1) {
       items::leaf_item<MIXED>(t, node, st, mp, mp32, loc, smem);
     } else {
       if (MIXED)
@@ -67,7 +77,10 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
 // Resident blocks per SM of a persistent variant (sets its shared-memory limit);
 // called once per handle, outside any stream capture.
 // Dynamic shared memory of the persistent kernel (the interior items use none).
-size_t persistent_smem_bytes(const Stencils& st, bool mixed) { return items::leaf_smem_bytes(st, mixed); }
+size_t persistent_smem_bytes(const Stencils& st, bool mixed) {
+  const size_t leaf = items::leaf_smem_bytes(st, mixed);
+  return mixed ? std::max(leaf, items::near_smem_bytes(st)) : leaf;
+}
 
 template <bool MIXED, int MINB>
 cudaError_t persistent_occupancy(const Stencils& st, int* per_sm) {
@@ -86,7 +99,7 @@ cudaError_t persistent_launch(const DevTree& t, const InteractArgs& a, cudaStrea
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_persistent<MIXED, MINB><<<a.grid, items::kThreads, smem, s>>>(t, a.queue, a.n_items, a.counter, a.st, a.mp,
-                                                                  a.mp32, a.loc);
+                                                                  a.mp32, a.loc, a.nearf, a.NL);
   return cudaGetLastError();
 }
 
@@ -136,15 +149,31 @@ cudaError_t launch_leaf_items(const DevTree& t, const InteractArgs& a, cudaStrea
   return cudaGetLastError();
 }
 
+cudaError_t launch_near_items(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
+  if (a.n_leaf == 0) return cudaSuccess;
+  k_near_items<<<a.n_leaf, items::kThreads, items::near_smem_bytes(a.st), s>>>(t, a.leaf, a.st, a.mp, a.nearf, a.NL);
+  return cudaGetLastError();
+}
+
+// Register budgets: 1 or 2 resident blocks per SM, and 3 in mixed precision (whose
+// items all fit 85 registers; the float64 interior item needs twice that).
 cudaError_t persistent_blocks_per_sm(bool mixed, int min_blocks, const Stencils& st, int* per_sm) {
-  if (mixed) return min_blocks == 2 ? persistent_occupancy<true, 2>(st, per_sm) : persistent_occupancy<true, 1>(st, per_sm);
+  if (mixed) {
+    if (min_blocks == 3) return persistent_occupancy<true, 3>(st, per_sm);
+    return min_blocks == 2 ? persistent_occupancy<true, 2>(st, per_sm) : persistent_occupancy<true, 1>(st, per_sm);
+  }
+  if (min_blocks == 3) return cudaErrorInvalidValue;
   return min_blocks == 2 ? persistent_occupancy<false, 2>(st, per_sm) : persistent_occupancy<false, 1>(st, per_sm);
 }
 
 cudaError_t launch_persistent(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
   if (a.n_items == 0) return cudaSuccess;
   if (a.grid < 1) return cudaErrorInvalidConfiguration;
-  if (a.mixed) return a.min_blocks == 2 ? persistent_launch<true, 2>(t, a, s) : persistent_launch<true, 1>(t, a, s);
+  if (a.mixed) {
+    if (a.min_blocks == 3) return persistent_launch<true, 3>(t, a, s);
+    return a.min_blocks == 2 ? persistent_launch<true, 2>(t, a, s) : persistent_launch<true, 1>(t, a, s);
+  }
+  if (a.min_blocks == 3) return cudaErrorInvalidValue;
   return a.min_blocks == 2 ? persistent_launch<false, 2>(t, a, s) : persistent_launch<false, 1>(t, a, s);
 }
 

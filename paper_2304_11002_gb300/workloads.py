@@ -355,10 +355,49 @@ def adaptive7(seed: int = 0) -> Workload:
     return adaptive_binary(6, 0.125, 0.7, seed, name="adaptive7")
 
 
-SWEEP = {  # target leaf subgrids -> (max level, R1 / L)
-    1000: (5, 0.11),
-    10000: (6, 0.155),
-    50000: (7, 0.145),
+def rotating_star(max_level: int, r_frac: float, seed: int = 0, extent: float = 1.0,
+                  name: Optional[str] = None) -> Workload:
+    """One n=1.5 polytrope of radius r_frac * extent at the domain centre (the rotating
+    star of the paper's distributed runs; rotation does not enter the gravity solve).
+    The seed shifts the star by a uniform offset below one finest cell.  Nodes are
+    refined where their box meets the rho > 1e-4 rho_c region, then 2:1 balanced;
+    the density has a 1e-10 floor outside the star."""
+    rng = np.random.default_rng(seed)
+    hf = extent / (8.0 * 2 ** max_level)
+    shift = rng.uniform(0.0, hf, size=3) if seed else np.zeros(3)
+    c = np.full(3, extent / 2.0) + shift
+    r = r_frac * extent
+    t = polytrope_threshold_radius(r, 1.0, 1e-4)
+
+    def box_refine(l, lo, hi):
+        p = np.clip(c, lo, hi)
+        return bool(np.sum((p - c) ** 2) < t * t)
+
+    tree = adaptive_tree(box_refine, max_level, extent)
+    x = tree.leaf_cell_centres()
+    rho = (polytrope_density(x, c, r, 1.0) + 1e-10).reshape(tree.n_leaf, 512)
+    nm = name or f"star{max_level}_s{seed}"
+    return Workload(nm, tree, rho, 0.5,
+                    f"rotating star, max level {max_level}, R={r_frac:g} L, seed {seed}, {tree.n_leaf} leaf subgrids")
+
+
+# max level -> star radius / L close to the paper's rotating-star sizes (5048, 27840
+# and 172208 subgrids at levels 5, 6, 7); seed 0 gives 5160, 27784, 169968 leaf subgrids
+STAR = {
+    5: 0.262,
+    6: 0.256,
+    7: 0.25,
+}
+
+
+def star(level: int, seed: int = 0) -> Workload:
+    return rotating_star(level, STAR[level], seed, name=f"star{level}")
+
+
+SWEEP = {  # target leaf subgrids -> (max level, R1 / L); q = 0.7, seed 0 gives 960 / 9976 / 50268
+    1000: (5, 0.075),
+    10000: (6, 0.137),
+    50000: (7, 0.133),
 }
 
 
@@ -379,4 +418,6 @@ RECIPES = {
 def make(name: str, **kw) -> Workload:
     if name.startswith("sweep"):
         return sweep(int(name[5:]), **kw)
+    if name.startswith("star"):
+        return star(int(name[4:]), **kw)
     return RECIPES[name](**kw)

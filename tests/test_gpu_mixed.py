@@ -47,9 +47,19 @@ def test_mixed_uniform16_full(seed):
     assert ephi <= TOL_MIXED and eg <= TOL_MIXED, (ephi, eg)
 
 
-@pytest.mark.parametrize("name", ["adaptive4", "binary64", "adaptive7"])
+def _workload(name):
+    """name or (sweep target, q, seed) of the throughput-sweep trees."""
+    if name == "adaptive4":
+        return W.adaptive_binary(3, 0.08)
+    if isinstance(name, tuple):
+        return W.sweep(name[0], q=name[1], seed=name[2])
+    return W.make(name)
+
+
+@pytest.mark.parametrize("name", ["adaptive4", "binary64", "adaptive7", (1000, 0.3, 1), (1000, 1.0, 2),
+                                  (10000, 0.7, 0), "star5"])
 def test_mixed_sampled(name):
-    w = W.adaptive_binary(3, 0.08) if name == "adaptive4" else W.make(name)
+    w = _workload(name)
     phi, g = _solve(w.tree, w.rho, binding.OCTO_MIXED)
     n = w.tree.n_leaf * 512
     rng = np.random.default_rng(6)

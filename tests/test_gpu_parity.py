@@ -114,12 +114,16 @@ def _sample(n_cells, k, seed):
     return idx, mask
 
 
-@pytest.mark.parametrize("name", ["adaptive4", "binary64", "adaptive7"])
+@pytest.mark.parametrize("name", ["adaptive4", "binary64", "adaptive7", (1000, 0.3, 1), (1000, 1.0, 2), "star5"])
 def test_sampled_cells_fp64(name):
     """Full-size trees (64^3 uniform binary; 7-level adaptive binary with ~8000
-    leaf subgrids): every cell computed on the GPU, a seeded sample of cells by
-    the oracle."""
-    w = W.adaptive_binary(3, 0.08) if name == "adaptive4" else W.make(name)
+    leaf subgrids; throughput-sweep trees of ~1000 leaf subgrids with mass ratios
+    0.3 and 1 and rotated axes): every cell computed on the GPU, a seeded sample of
+    cells by the oracle."""
+    if isinstance(name, tuple):
+        w = W.sweep(name[0], q=name[1], seed=name[2])
+    else:
+        w = W.adaptive_binary(3, 0.08) if name == "adaptive4" else W.make(name)
     fmm, phi, g = _run(w.tree, w.rho)
     idx, mask = _sample(w.tree.n_leaf * 512, 192, 5)
     po, go, _ = oracle.fmm(w.tree, w.rho, leaf_mask=mask)
@@ -191,12 +195,13 @@ def test_errors_are_reported():
 
 @pytest.mark.parametrize("precision", [binding.OCTO_FP64, binding.OCTO_MIXED])
 def test_interaction_strategies_bit_identical(precision):
-    """Per-kind launches and the persistent work queue (both register budgets) run
+    """Per-kind launches and the persistent work queue (every register budget) run
     the same item functions: identical results, and the autotuner picks one of them."""
     w = W.adaptive_binary(3, 0.08)
     r = torch.from_numpy(w.rho.reshape(-1).copy()).cuda()
     outs = []
-    for mode, minb in ((1, 1), (2, 1), (2, 2)):
+    budgets = (1, 2, 3) if precision == binding.OCTO_MIXED else (1, 2)
+    for mode, minb in [(1, 1)] + [(2, b) for b in budgets]:
         fmm = binding.OctoFMM(w.tree, 0.5, precision)
         binding.octo_fmm_set_option(fmm.handle, 3, mode)
         binding.octo_fmm_set_option(fmm.handle, 4, minb)
@@ -207,5 +212,9 @@ def test_interaction_strategies_bit_identical(precision):
     fmm = binding.OctoFMM(w.tree, 0.5, precision)
     phi, g = fmm.forces(r)
     assert binding.octo_fmm_get_option(fmm.handle, 3) in (1, 2)
-    assert all(binding.octo_fmm_get_option(fmm.handle, k) > 0 for k in (10, 11, 12))
+    assert all(binding.octo_fmm_get_option(fmm.handle, k) > 0 for k in [10 + b for b in (0,) + budgets])
+    if precision == binding.OCTO_FP64:
+        assert binding.octo_fmm_get_option(fmm.handle, 13) == 0
+        with pytest.raises(binding.OctoError):
+            binding.octo_fmm_set_option(fmm.handle, 4, 3)
     assert torch.equal(phi, outs[0][0]) and torch.equal(g, outs[0][1])
