@@ -304,22 +304,31 @@ __device__ __forceinline__ void stage_halo(const HaloGeom& g, const int* nleaf, 
 
 // Leaf neighbour table of `node` into shared memory; returns whether any same-level
 // neighbour is refined (block-uniform).  Ends with a barrier.
-__device__ __forceinline__ bool load_leaf_neighbours(const DevTree& t, int node, int* nleaf, int* any_refined) {
+__device__ __forceinline__ bool load_leaf_neighbours(const DevTree& t, int node, int* nleaf) {
   __syncthreads();  // the previous item may still read shared memory
+  bool refined = false;
   if (threadIdx.x < 27) {
     const int sn = t.nbr[27 * node + threadIdx.x];
-    nleaf[threadIdx.x] = sn >= 0 && t.children[8 * sn] < 0 ? sn : -1;
+    refined = sn >= 0 && t.children[8 * sn] >= 0;
+    nleaf[threadIdx.x] = sn >= 0 && !refined ? sn : -1;
   }
-  if (threadIdx.x == 0) {
-    int any = 0;
-    for (int o = 0; o < 27; ++o) {
-      const int sn = t.nbr[27 * node + o];
-      any |= sn >= 0 && t.children[8 * sn] >= 0;
-    }
-    *any_refined = any;
+  return __syncthreads_or(refined) != 0;
+}
+
+// Local index of the q-th (q = 0, 1) cell owned by thread tid in a leaf item.
+// Mixed path: warp w holds parity class w, lane (i, j, k0) the cells
+// (2i + pa, 2j + pb, 2 (k0 + 2q) + pc).  Float64 path: cell_of(q, tid).
+template <bool MIXED>
+__host__ __device__ __forceinline__ int leaf_cell(int q, int tid) {
+  if (MIXED) {
+    const int p = tid >> 5, lane = tid & 31;
+    const int a = 2 * (lane & 3) + (p & 1), b = 2 * ((lane >> 2) & 3) + ((p >> 1) & 1);
+    const int c = 2 * ((lane >> 4) + 2 * q) + (p >> 2);
+    return a + 8 * b + 64 * c;
   }
-  __syncthreads();
-  return *any_refined != 0;
+  int p, zh, a, b, c;
+  cell_of(q, tid, p, zh, a, b, c);
+  return a + 8 * b + 64 * c;
 }
 
 // One leaf node per block (both halves): stage the halo once, then every thread
@@ -332,8 +341,7 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
                                           double* __restrict__ loc, unsigned char* smem) {
   const HaloGeom gf = far_geom(st.radius);
   __shared__ int nleaf[27];
-  __shared__ int any_refined_s;
-  const bool any_refined = load_leaf_neighbours(t, node, nleaf, &any_refined_s);
+  const bool any_refined = load_leaf_neighbours(t, node, nleaf);
   float* halo32 = reinterpret_cast<float*>(smem);
   double* halo64 = reinterpret_cast<double*>(smem);
   if (MIXED)
@@ -344,41 +352,54 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
   const int lvl = t.level[node];
   const int n_far = lvl == 0 ? st.n_root : st.n_st;
   const double ih = 1.0 / t.h[lvl], ih2 = ih * ih;
-  double L0[2], L1[2][3];
+  double L0[2], L1[2][3];  // the thread's two cells (see leaf_cell)
+  if (MIXED) {
+    // warp w = parity class w; lane (i, j, k0) owns the cells with c / 2 = k0 and
+    // k0 + 2: both share every stencil entry (one table and one kernel load feed
+    // two halo reads and eight fused multiply-adds)
+    const int lane = threadIdx.x & 31;
+    const int2* __restrict__ far = (lvl == 0 ? st.leaf_root : st.leaf_far) + (threadIdx.x >> 5) * n_far;
+    const int lane_f = (lane & 3) + gf.PY * ((lane >> 2) & 3) + gf.PZ * (lane >> 4);
+    const int dz = 2 * gf.PZ;
+    KF f[2][4];
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    int p, zh, a, b, c;
-    cell_of(half, threadIdx.x, p, zh, a, b, c);
-    const int2* __restrict__ far = (lvl == 0 ? st.leaf_root : st.leaf_far) + p * n_far;
-    const int2* __restrict__ nr = st.leaf_near + p * st.n_near;
-    const int lane_f = (a >> 1) + gf.PY * (b >> 1) + gf.PZ * (c >> 1);
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // float64 sums, unit cell width
-    if (MIXED) {
-      KF f0, f1, f2, f3;
-      f0 = 0.0f, f1 = 0.0f, f2 = 0.0f, f3 = 0.0f;
-      for (int s0i = 0; s0i < n_far; s0i += kAccBlock) {
-        const int s1i = min(s0i + kAccBlock, n_far);
-        float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f[q][k] = 0.0f;
+    for (int s0i = 0; s0i < n_far; s0i += kAccBlock) {
+      const int s1i = min(s0i + kAccBlock, n_far);
+      float pa[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
-        for (int s = s0i; s < s1i; ++s) {
-          const int2 e = __ldg(far + s);
-          const float m = halo32[lane_f + e.x];
-          const float4 k = __ldg(st.kappa32 + e.y);
-          p0 = fmaf(m, k.x, p0);
-          p1 = fmaf(m, k.y, p1);
-          p2 = fmaf(m, k.z, p2);
-          p3 = fmaf(m, k.w, p3);
-        }
-        f0.add(p0);
-        f1.add(p1);
-        f2.add(p2);
-        f3.add(p3);
+      for (int s = s0i; s < s1i; ++s) {
+        const int2 e = __ldg(far + s);
+        const float m0 = halo32[lane_f + e.x], m1 = halo32[lane_f + e.x + dz];
+        const float4 k = __ldg(st.kappa32 + e.y);
+        pa[0] = fmaf(m0, k.x, pa[0]);
+        pa[1] = fmaf(m0, k.y, pa[1]);
+        pa[2] = fmaf(m0, k.z, pa[2]);
+        pa[3] = fmaf(m0, k.w, pa[3]);
+        pb[0] = fmaf(m1, k.x, pb[0]);
+        pb[1] = fmaf(m1, k.y, pb[1]);
+        pb[2] = fmaf(m1, k.z, pb[2]);
+        pb[3] = fmaf(m1, k.w, pb[3]);
       }
-      s0 = f0.value();
-      s1 = f1.value();
-      s2 = f2.value();
-      s3 = f3.value();
-    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f[0][k].add(pa[k]), f[1][k].add(pb[k]);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      L0[q] = f[q][0].value() * ih;
+      for (int i = 0; i < 3; ++i) L1[q][i] = f[q][1 + i].value() * ih2;
+    }
+  } else {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      int p, zh, a, b, c;
+      cell_of(half, threadIdx.x, p, zh, a, b, c);
+      const int2* __restrict__ far = (lvl == 0 ? st.leaf_root : st.leaf_far) + p * n_far;
+      const int2* __restrict__ nr = st.leaf_near + p * st.n_near;
+      const int lane_f = (a >> 1) + gf.PY * (b >> 1) + gf.PZ * (c >> 1);
+      double s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // unit cell width
       for (int pass = 0; pass < 2; ++pass) {
         const int2* __restrict__ tb = pass == 0 ? far : nr;
         const int nt = pass == 0 ? n_far : st.n_near;
@@ -393,11 +414,11 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
           s3 = fma(m, kb.y, s3);
         }
       }
+      L0[half] = s0 * ih;
+      L1[half][0] = s1 * ih2;
+      L1[half][1] = s2 * ih2;
+      L1[half][2] = s3 * ih2;
     }
-    L0[half] = s0 * ih;
-    L1[half][0] = s1 * ih2;
-    L1[half][1] = s2 * ih2;
-    L1[half][2] = s3 * ih2;
   }
   double dg[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
   if (any_refined) {  // block-uniform
@@ -427,22 +448,18 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
     }
     __syncthreads();
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      int p, zh, a, b, c;
-      cell_of(half, threadIdx.x, p, zh, a, b, c);
-      const int l = a + 8 * b + 64 * c;
-      L0[half] += res[l * 7];
-      for (int i = 0; i < 3; ++i) L1[half][i] += res[l * 7 + 1 + i], dg[half][i] = res[l * 7 + 4 + i];
+    for (int q = 0; q < 2; ++q) {
+      const int l = leaf_cell<MIXED>(q, threadIdx.x);
+      L0[q] += res[l * 7];
+      for (int i = 0; i < 3; ++i) L1[q][i] += res[l * 7 + 1 + i], dg[q][i] = res[l * 7 + 4 + i];
     }
   }
   const int64_t NC = t.NC;
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    int p, zh, a, b, c;
-    cell_of(half, threadIdx.x, p, zh, a, b, c);
-    const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
-    loc[G_L0 * NC + tgt] = L0[half];
-    for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = L1[half][i], loc[(G_DG + i) * NC + tgt] = dg[half][i];
+  for (int q = 0; q < 2; ++q) {
+    const int64_t tgt = (int64_t)node * 512 + leaf_cell<MIXED>(q, threadIdx.x);
+    loc[G_L0 * NC + tgt] = L0[q];
+    for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] = L1[q][i], loc[(G_DG + i) * NC + tgt] = dg[q][i];
   }
 }
 
@@ -456,8 +473,7 @@ __device__ __forceinline__ void near_item(const DevTree& t, int node, const Sten
                                           unsigned char* smem) {
   const HaloGeom gn = near_geom(st.near_radius);
   __shared__ int nleaf_n[27];
-  __shared__ int any_refined_n;
-  load_leaf_neighbours(t, node, nleaf_n, &any_refined_n);
+  load_leaf_neighbours(t, node, nleaf_n);
   double* halo = reinterpret_cast<double*>(smem);
   stage_halo(gn, nleaf_n, mp, halo);
   __syncthreads();
