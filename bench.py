@@ -235,9 +235,9 @@ def roofline_of(info, mean_stage_ms, peaks):
 
 
 def stage_rates(info, mean_stage_ms, peaks):
-    """Per stage: time, and either the float32 / float64 flop rates as fractions of
-    their peaks (interaction stages) or HBM GB/s as a fraction of the measured copy
-    bandwidth (tree passes; algorithmic bytes, every value read or written once)."""
+    """Per stage: time, the float32 / float64 flop rates as fractions of their peaks,
+    and for the tree passes also HBM GB/s as a fraction of the measured copy
+    bandwidth (algorithmic bytes, every value read or written once)."""
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     out = {}
     for i, st in enumerate(info):
@@ -250,7 +250,7 @@ def stage_rates(info, mean_stage_ms, peaks):
             f32 = st["flops"] - f64
             d["fp32_frac"] = round(f32 / (ms / 1e3) / 1e12 / PEAK_FP32_TFLOPS, 4)
             d["fp64_frac"] = round(f64 / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS, 4)
-        elif st["bytes"] > 0:
+        if st["bytes"] > 0:
             gbs = st["bytes"] / (ms / 1e3) / 1e9
             d["gbs"] = round(gbs, 1)
             d["hbm_frac"] = round(gbs / hbm, 4)

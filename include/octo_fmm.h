@@ -99,10 +99,10 @@ int octo_fmm_downward(octo_fmm_t h, double* phi_dev, double* g_dev, void* stream
  * captured on first use for this stream. */
 int octo_fmm_forces(octo_fmm_t h, const double* rho_dev, double* phi_dev, double* g_dev, void* stream);
 
-/* The same solve with HOST buffers: copies rho in and phi, g out on `stream`
- * through pinned staging buffers owned by the handle, and synchronises the stream
- * before returning.  rho_host [n_leaf*512], phi_host [n_leaf*512],
- * g_host [3][n_leaf*512]. */
+/* The same solve with HOST buffers (ordinary pageable memory is fine): copies rho
+ * in and phi, g out on `stream` between the caller's buffers and device buffers
+ * owned by the handle, and synchronises the stream before returning.
+ * rho_host [n_leaf*512], phi_host [n_leaf*512], g_host [3][n_leaf*512]. */
 int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host, double* g_host, void* stream);
 
 /* Vector-Jacobian product of the last forces/upward+interact+downward solve on this

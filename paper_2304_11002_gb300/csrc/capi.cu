@@ -128,7 +128,7 @@ struct octo_fmm {
   bool use_graph = true;
 
   // host-buffer path
-  double *h_stage = nullptr, *d_io = nullptr;
+  double* d_io = nullptr;
 
   // the solve as a fixed list of stages, one kernel launch each
   struct Stage {
@@ -180,7 +180,6 @@ void free_all(octo_fmm* h) {
   for (CrossSet* cs : {&h->xg, &h->xb})
     for (int64_t* p : {cs->d_ft, cs->d_fs, cs->d_fm, cs->d_fsrc, cs->d_lt, cs->d_ls, cs->d_lm, cs->d_lsrc})
       if (p) cudaFree(p);
-  if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto& ev : h->ev)
@@ -229,6 +228,13 @@ int64_t m2l_pair_flops() {
   return g_counted_ops + 3 + 5 + 8;
 }
 constexpr int64_t kConvFlopsPerPair = 8;  // four fused multiply-adds
+// Tree passes, float64 in both modes, counted from the expressions of k_m2m / k_l2l
+// as written (FMA = 2): M2M per parent cell = 8 children x (mass and centre sums 7,
+// d 3, m d 3, M2 18, M3 64) + 3 divisions; L2L per cell = d 3, (L3 d) 30, (L3 d d)
+// 15, (L2 d) 15, L0 21, L1 12, dg 3, plus L2 / L3 updates 22 at refined cells or
+// L2P (g, near field) 7 at leaf cells.
+constexpr int64_t kM2MFlopsPerCell = 8 * (7 + 3 + 3 + 18 + 64) + 3;
+constexpr int64_t kL2LFlopsInterior = 99 + 22, kL2LFlopsLeaf = 99 + 7;
 // exact point-mass pair: R (3), r^2 (5), reciprocal square root (8), m/r, m/r^3 (3), phi and g (7)
 constexpr int64_t kP2PFlopsPerPair = 26;
 
@@ -243,7 +249,10 @@ void make_stages(octo_fmm* h) {
     const int64_t f_int = m2l_pair_flops<true, true>(), f_leaf = m2l_pair_flops<false, false>();
     switch (kind) {
       case S_P2M: bytes = cells * 16; break;                      // rho in, m out
-      case S_M2M: bytes = cells * (8 * 20 + 20) * 8; break;        // 8 children in, parent out
+      case S_M2M:                                                  // 8 children in, parent out
+        bytes = cells * (8 * 20 + 20) * 8;
+        near = cells * kM2MFlopsPerCell;
+        break;
       case S_M2L: far = pairs * f_int; break;
       case S_CONV:  // mixed precision: the near field is the separate S_NEAR stage
         far = P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
@@ -263,7 +272,13 @@ void make_stages(octo_fmm* h) {
         far = (pairs - h->xg.l_p2p) * f_leaf;
         near = h->xg.l_p2p * kP2PFlopsPerPair;
         break;
-      case S_L2L: bytes = cells * 52 * 8; break;                   // own L/X in + L out + parent share
+      case S_L2L: {  // own L/X in + L out + parent share
+        bytes = cells * 52 * 8;
+        int64_t leaf_cells = 0;
+        for (int k = a; k < b; ++k) leaf_cells += P.children[8 * k] < 0 ? kCells : 0;
+        near = leaf_cells * kL2LFlopsLeaf + (cells - leaf_cells) * kL2LFlopsInterior;
+        break;
+      }
     }
     const int64_t flops = far + near;
     const int64_t flops64 = h->precision == OCTO_MIXED ? near : flops;
@@ -554,7 +569,6 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   if (e == cudaSuccess && precision == OCTO_MIXED) e = cudaMalloc(&h->d_mp32, sizeof(float) * N_MP * NC);
   if (e == cudaSuccess && precision == OCTO_MIXED) e = cudaMalloc(&h->d_near, sizeof(double) * 4 * h->n_leaf_cells());
   if (e == cudaSuccess) e = cudaMalloc(&h->d_io, sizeof(double) * 5 * h->n_leaf_cells());
-  if (e == cudaSuccess) e = cudaMallocHost(&h->h_stage, sizeof(double) * 5 * h->n_leaf_cells());
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     std::string m = std::string("device setup failed: ") + cudaGetErrorString(e);
@@ -763,16 +777,17 @@ int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host,
   double* d_rho = h->d_io;
   double* d_phi = h->d_io + n;
   double* d_g = h->d_io + 2 * n;
-  std::memcpy(h->h_stage, rho_host, sizeof(double) * n);
-  cudaError_t e = cudaMemcpyAsync(d_rho, h->h_stage, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  // Straight between the caller's (pageable) buffers and the device: on a Grace host
+  // the copy engines read and write pageable memory through the coherent link at the
+  // same rate as pinned memory, so a host-side staging copy would only add time.
+  cudaError_t e = cudaMemcpyAsync(d_rho, rho_host, sizeof(double) * n, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "copy rho in");
   int rc = octo_fmm_forces(h, d_rho, d_phi, d_g, stream);
   if (rc != OCTO_OK) return rc;
-  e = cudaMemcpyAsync(h->h_stage + n, d_phi, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(phi_host, d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g_host, d_g, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "copy results out");
-  std::memcpy(phi_host, h->h_stage + n, sizeof(double) * n);
-  std::memcpy(g_host, h->h_stage + 2 * n, sizeof(double) * 3 * n);
   return OCTO_OK;
 }
 

@@ -280,24 +280,31 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
 template <typename T>
 __device__ __forceinline__ void stage_halo(const HaloGeom& g, const int* nleaf, const double* __restrict__ mp,
                                            T* halo) {
-  constexpr int kStage = 4;  // independent loads in flight per thread before their stores
-  const int H = 2 * g.G, R = g.r, n_halo = H * H * H;
-  for (int i0 = threadIdx.x; i0 < n_halo; i0 += kStage * blockDim.x) {
-    double m[kStage];
+  // one halo row (fixed y, z) per warp and step, lanes along x (consecutive cells of
+  // a neighbour's row are contiguous in memory); kRows rows of loads in flight
+  constexpr int kRows = 4;
+  const int H = 2 * g.G, R = g.r, n_rows = H * H;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  for (int x0 = 0; x0 < H; x0 += 32) {
+    const int hx = x0 + lane;
+    const int x = hx - R;
+    for (int r0 = warp; r0 < n_rows; r0 += kRows * n_warps) {
+      double m[kRows];
 #pragma unroll
-    for (int u = 0; u < kStage; ++u) {
-      const int i = i0 + u * blockDim.x;
-      m[u] = 0.0;
-      if (i < n_halo) {
-        const int x = i % H - R, y = (i / H) % H - R, z = i / (H * H) - R;
-        const int sn = nleaf[((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1)];
-        if (sn >= 0) m[u] = __ldg(mp + (int64_t)sn * 512 + (x & 7) + 8 * (y & 7) + 64 * (z & 7));
+      for (int u = 0; u < kRows; ++u) {
+        const int r = r0 + u * n_warps;
+        m[u] = 0.0;
+        if (r < n_rows && hx < H) {
+          const int y = r % H - R, z = r / H - R;
+          const int sn = nleaf[((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1)];
+          if (sn >= 0) m[u] = __ldg(mp + (int64_t)sn * 512 + (x & 7) + 8 * (y & 7) + 64 * (z & 7));
+        }
       }
-    }
 #pragma unroll
-    for (int u = 0; u < kStage; ++u) {
-      const int i = i0 + u * blockDim.x;
-      if (i < n_halo) halo[halo_index(g, i % H, (i / H) % H, i / (H * H))] = (T)m[u];
+      for (int u = 0; u < kRows; ++u) {
+        const int r = r0 + u * n_warps;
+        if (r < n_rows && hx < H) halo[halo_index(g, hx, r % H, r / H)] = (T)m[u];
+      }
     }
   }
 }

@@ -47,8 +47,10 @@ __global__ void k_p2m(DevTree t, const int* __restrict__ nodes, const double* __
 // Parent cell from its 2x2x2 child cells (parallel-axis rule about the centre of
 // mass): m = sum m_c, X = sum m_c X_c / m, d_c = X_c - X,
 // M2 = sum (M2_c + m_c d d), M3 = sum (M3_c + 3 sym(M2_c d) + m_c d d d).
-__global__ void __launch_bounds__(256) k_m2m(DevTree t, int node_begin, double* __restrict__ mp,
-                                             float* __restrict__ mp32) {
+// (registers capped for 3 resident blocks per SM so that enough warps keep loads
+// in flight; the children loop of the moments stays rolled)
+__global__ void __launch_bounds__(256, 3) k_m2m(DevTree t, int node_begin, double* __restrict__ mp,
+                                                float* __restrict__ mp32) {
   const int node = node_begin + (blockIdx.x >> 1);
   if (t.children[8 * node] < 0) return;
   const int l = ((blockIdx.x & 1) << 8) + threadIdx.x;
@@ -56,30 +58,32 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int node_begin, double* 
   const int o = (a >> 2) + 2 * (b >> 2) + 4 * (c >> 2);
   const int ch = t.children[8 * node + o];
   const int64_t NC = t.NC;
-  int64_t cc[8];
-  for (int e = 0; e < 8; ++e) {
-    const int ca = 2 * (a & 3) + (e & 1), cb = 2 * (b & 3) + ((e >> 1) & 1), cz = 2 * (c & 3) + (e >> 2);
-    cc[e] = (int64_t)ch * 512 + ca + 8 * cb + 64 * cz;
-  }
+  // child cell e = ex + 2 ey + 4 ez of this parent cell
+  const int64_t c0 = (int64_t)ch * 512 + 2 * (a & 3) + 8 * 2 * (b & 3) + 64 * 2 * (c & 3);
+  auto child = [c0](int e) { return c0 + (e & 1) + 8 * ((e >> 1) & 1) + 64 * (e >> 2); };
   double m = 0, X0 = 0, X1 = 0, X2 = 0;
-  for (int e = 0; e < 8; ++e) m += mp[cc[e]];
+#pragma unroll
   for (int e = 0; e < 8; ++e) {
-    const double mc = mp[cc[e]];
-    X0 += mc * mp[(F_X + 0) * NC + cc[e]];
-    X1 += mc * mp[(F_X + 1) * NC + cc[e]];
-    X2 += mc * mp[(F_X + 2) * NC + cc[e]];
+    const int64_t ce = child(e);
+    const double mc = mp[ce];
+    m += mc;
+    X0 += mc * mp[(F_X + 0) * NC + ce];
+    X1 += mc * mp[(F_X + 1) * NC + ce];
+    X2 += mc * mp[(F_X + 2) * NC + ce];
   }
   X0 /= m;
   X1 /= m;
   X2 /= m;
   double Q[6] = {0, 0, 0, 0, 0, 0}, O[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 1
   for (int e = 0; e < 8; ++e) {
-    const double mc = mp[cc[e]];
-    const double d0 = mp[(F_X + 0) * NC + cc[e]] - X0;
-    const double d1 = mp[(F_X + 1) * NC + cc[e]] - X1;
-    const double d2 = mp[(F_X + 2) * NC + cc[e]] - X2;
+    const int64_t ce = child(e);
+    const double mc = mp[ce];
+    const double d0 = mp[(F_X + 0) * NC + ce] - X0;
+    const double d1 = mp[(F_X + 1) * NC + ce] - X1;
+    const double d2 = mp[(F_X + 2) * NC + ce] - X2;
     double q[6];
-    for (int i = 0; i < 6; ++i) q[i] = mp[(F_Q + i) * NC + cc[e]];
+    for (int i = 0; i < 6; ++i) q[i] = mp[(F_Q + i) * NC + ce];
     const double md0 = mc * d0, md1 = mc * d1, md2 = mc * d2;
     Q[0] += q[0] + md0 * d0;
     Q[1] += q[1] + md0 * d1;
@@ -88,16 +92,16 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int node_begin, double* 
     Q[4] += q[4] + md1 * d2;
     Q[5] += q[5] + md2 * d2;
     // 3 sym(q d)_abc = q_ab d_c + q_ac d_b + q_bc d_a
-    O[0] += mp[(F_O + 0) * NC + cc[e]] + 3.0 * q[0] * d0 + md0 * d0 * d0;                    // xxx
-    O[1] += mp[(F_O + 1) * NC + cc[e]] + q[0] * d1 + 2.0 * q[1] * d0 + md0 * d0 * d1;        // xxy
-    O[2] += mp[(F_O + 2) * NC + cc[e]] + q[0] * d2 + 2.0 * q[2] * d0 + md0 * d0 * d2;        // xxz
-    O[3] += mp[(F_O + 3) * NC + cc[e]] + 2.0 * q[1] * d1 + q[3] * d0 + md0 * d1 * d1;        // xyy
-    O[4] += mp[(F_O + 4) * NC + cc[e]] + q[1] * d2 + q[2] * d1 + q[4] * d0 + md0 * d1 * d2;  // xyz
-    O[5] += mp[(F_O + 5) * NC + cc[e]] + 2.0 * q[2] * d2 + q[5] * d0 + md0 * d2 * d2;        // xzz
-    O[6] += mp[(F_O + 6) * NC + cc[e]] + 3.0 * q[3] * d1 + md1 * d1 * d1;                    // yyy
-    O[7] += mp[(F_O + 7) * NC + cc[e]] + q[3] * d2 + 2.0 * q[4] * d1 + md1 * d1 * d2;        // yyz
-    O[8] += mp[(F_O + 8) * NC + cc[e]] + 2.0 * q[4] * d2 + q[5] * d1 + md1 * d2 * d2;        // yzz
-    O[9] += mp[(F_O + 9) * NC + cc[e]] + 3.0 * q[5] * d2 + md2 * d2 * d2;                    // zzz
+    O[0] += mp[(F_O + 0) * NC + ce] + 3.0 * q[0] * d0 + md0 * d0 * d0;                    // xxx
+    O[1] += mp[(F_O + 1) * NC + ce] + q[0] * d1 + 2.0 * q[1] * d0 + md0 * d0 * d1;        // xxy
+    O[2] += mp[(F_O + 2) * NC + ce] + q[0] * d2 + 2.0 * q[2] * d0 + md0 * d0 * d2;        // xxz
+    O[3] += mp[(F_O + 3) * NC + ce] + 2.0 * q[1] * d1 + q[3] * d0 + md0 * d1 * d1;        // xyy
+    O[4] += mp[(F_O + 4) * NC + ce] + q[1] * d2 + q[2] * d1 + q[4] * d0 + md0 * d1 * d2;  // xyz
+    O[5] += mp[(F_O + 5) * NC + ce] + 2.0 * q[2] * d2 + q[5] * d0 + md0 * d2 * d2;        // xzz
+    O[6] += mp[(F_O + 6) * NC + ce] + 3.0 * q[3] * d1 + md1 * d1 * d1;                    // yyy
+    O[7] += mp[(F_O + 7) * NC + ce] + q[3] * d2 + 2.0 * q[4] * d1 + md1 * d1 * d2;        // yyz
+    O[8] += mp[(F_O + 8) * NC + ce] + 2.0 * q[4] * d2 + q[5] * d1 + md1 * d2 * d2;        // yzz
+    O[9] += mp[(F_O + 9) * NC + ce] + 3.0 * q[5] * d2 + md2 * d2 * d2;                    // zzz
   }
   const int64_t pc = (int64_t)node * 512 + l;
   mp[pc] = m;
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(256) k_m2m(DevTree t, int node_begin, double* 
 // (exact for the cubic Taylor polynomial), dg carried down unshifted.  At leaf
 // nodes the result is evaluated at the cell itself (L2P):
 //   phi = L0,  g = -L1 + dg  (plus the near-field sums when they are kept apart).
-__global__ void __launch_bounds__(256) k_l2l(DevTree t, int node_begin, const double* __restrict__ mp,
+__global__ void __launch_bounds__(256, 2) k_l2l(DevTree t, int node_begin, const double* __restrict__ mp,
                                              double* __restrict__ loc, double* __restrict__ phi,
                                              double* __restrict__ g, int64_t NL,
                                              const double* __restrict__ nearf) {
