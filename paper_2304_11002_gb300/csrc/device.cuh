@@ -145,7 +145,7 @@ __host__ __device__ __forceinline__ void m2l_pair(const T R0, const T R1, const 
   a.L1[0] -= c1 * R0 + f2 * QR0;
   a.L1[1] -= c1 * R1 + f2 * QR1;
   a.L1[2] -= c1 * R2 + f2 * QR2;
-  if (FULL) {
+  if constexpr (FULL) {
     const T mf2 = m * f2;
     a.L2[0] -= mf2 * xx;
     a.L2[1] -= mf2 * xy;
@@ -172,7 +172,7 @@ __host__ __device__ __forceinline__ void m2l_pair(const T R0, const T R1, const 
   }
   // correction with C = m Oh - O
   T cS, cT, v0, v1, v2, w0, w1, w2;
-  if (TOCT) {
+  if constexpr (TOCT) {
     const T uA0 = Oh[0] * xx + Oh[1] * xy2 + Oh[2] * xz2 + Oh[3] * yy + Oh[4] * yz2 + Oh[5] * zz;
     const T uA1 = Oh[1] * xx + Oh[3] * xy2 + Oh[4] * xz2 + Oh[6] * yy + Oh[7] * yz2 + Oh[8] * zz;
     const T uA2 = Oh[2] * xx + Oh[4] * xy2 + Oh[5] * xz2 + Oh[7] * yy + Oh[8] * yz2 + Oh[9] * zz;

@@ -222,9 +222,31 @@ __host__ __device__ inline size_t near_smem_bytes(const Stencils& st) {
   return sizeof(double) * 8 * (size_t)near_geom(st.near_radius).PQ;
 }
 
+// Accumulator of a leaf target (m2l_pair<false, ...> touches only L0, L1, dg).
+template <typename T>
+struct LeafAcc {
+  T L0, L1[3], dg[3];
+};
+
+// Compensated merge of float32 partial sums into acc (Acc<KF>); zeroes the partials.
+template <typename A>
+__device__ __forceinline__ void leaf_merge(A& acc, LeafAcc<float>& p) {
+  acc.L0.add(p.L0);
+  p.L0 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    acc.L1[i].add(p.L1[i]);
+    acc.dg[i].add(p.dg[i]);
+    p.L1[i] = 0.0f;
+    p.dg[i] = 0.0f;
+  }
+}
+
 // M2L from refined same-level neighbours into leaf cell l of a leaf node (leaf
 // target: L0, L1, dg).  The per-cell entry lists hold only offsets whose source
 // lies in the neighbour slot, so every iteration of every lane is a valid pair.
+// Mixed path: plain float32 partial sums of kAccBlock pairs merged into the
+// compensated sums of acc (Acc<KF>).
 template <bool MIXED, typename A>
 __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l, const Stencils& st,
                                                const double* __restrict__ mp, const float* __restrict__ mp32,
@@ -242,6 +264,9 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
     xA0 = mp[(F_X + 0) * NC + tgt], xA1 = mp[(F_X + 1) * NC + tgt], xA2 = mp[(F_X + 2) * NC + tgt];
   }
   const T zero10[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // mixed path: partial sums of L0, L1, dg (the only fields a leaf target gets)
+  LeafAcc<float> part = {0.0f, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+  int n_part = 0;
   for (int o = 0; o < 27; ++o) {
     const int sn = nb[o];
     if (sn < 0 || t.children[8 * sn] < 0) continue;  // refined neighbours only
@@ -269,9 +294,18 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
         for (int i = 0; i < 10; ++i) O[i] = __ldg(mp + (F_O + i) * NC + src);
         rinv = rsqrt_f64(fma(R0, R0, fma(R1, R1, R2 * R2)));
       }
-      m2l_pair<false, false>(R0, R1, R2, m, Q, O, zero10, zero10, rinv, acc);
+      if constexpr (MIXED) {
+        m2l_pair<false, false>(R0, R1, R2, m, Q, O, zero10, zero10, rinv, part);
+        if (++n_part == kAccBlock) {
+          leaf_merge(acc, part);
+          n_part = 0;
+        }
+      } else {
+        m2l_pair<false, false>(R0, R1, R2, m, Q, O, zero10, zero10, rinv, acc);
+      }
     }
   }
+  if constexpr (MIXED) leaf_merge(acc, part);
 }
 
 // Stages the masses of the leaf same-level neighbourhood of `node` (cells within
