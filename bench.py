@@ -110,6 +110,38 @@ def dist_env():
     return ws, rank, local
 
 
+# DRAM traffic of the roofline kernel comes from one ncu capture (profiles/
+# roofline_traffic.json); it is reported only while the kernel sources are those the
+# capture was taken with (sha256 over these files), else null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+KERNEL_SOURCES = ("capi.cu", "device.cuh", "items.cuh", "kernels.h", "kernels_boundary.cu", "kernels_interact.cu")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2304_11002_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(stage: str, workload: str):
+    """(bytes per launch, source) of a matching capture, or (None, reason)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            entries = json.load(f)["entries"]
+    except Exception:
+        return None, "no capture recorded"
+    sha = kernel_sources_sha256()
+    for e in entries:
+        if e["stage"] == stage and e["workload"] == workload:
+            if e["sources_sha256"] == sha:
+                return int(e["bytes"]), e["command"]
+            return None, "kernel changed since the capture"
+    return None, "no capture for this kernel and workload"
+
+
 def aggregate_over_ranks(t_rank_s: float, units_per_step: float, steps: int, ws: int, reduce_max=None):
     """Whole-job throughput of ws replicas (each rank solves the same workload on its
     own GPU): units all ranks processed over the slowest rank's time.  reduce_max
@@ -317,6 +349,7 @@ def run_ours(args):
     # dominant kernel of the step and its roofline
     mean_stage = stage_ms.mean(axis=0)
     roof = roofline_of(info, mean_stage, _measured_peaks())
+    roof["traffic"], roof["traffic_source"] = recorded_traffic(roof["kernel"], w.name)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     nlc = fmm.n_leaf_cells
@@ -346,13 +379,30 @@ def run_ours(args):
 
     if precision == binding.OCTO_MIXED and not args.no_fp64:
         del fmm
-        _, info64, s_ms, st_ms, _, _ = time_solver(w, binding.OCTO_FP64, max(3, args.steps // 2), 3, torch, flush,
-                                                   stream, args.strategy)
+        fmm64, info64, s_ms, st_ms, _, bufs64 = time_solver(w, binding.OCTO_FP64, max(3, args.steps // 2), 3, torch,
+                                                            flush, stream, args.strategy)
         m64 = st_ms.mean(axis=0)
+        # the hand-written adjoint (d loss / d rho for given d loss / d phi, d loss / d g)
+        # after the last forward solve of this handle
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        dphi = torch.randn(nlc, dtype=torch.float64, device="cuda", generator=gen)
+        dg = torch.randn((3, nlc), dtype=torch.float64, device="cuda", generator=gen)
+        drho = torch.empty(nlc, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            binding.octo_fmm_backward(fmm64.handle, dphi, dg, drho, stream)  # allocates the adjoint workspace
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            for _ in range(3):
+                binding.octo_fmm_backward(fmm64.handle, dphi, dg, drho, stream)
+            b1.record(stream)
+            stream.synchronize()
+        backward_ms = b0.elapsed_time(b1) / 3.0
+        del fmm64, bufs64
         fp64 = {"value": n_inter / (float(np.mean(s_ms)) / 1e3), "ms_per_step": float(np.mean(s_ms)),
                 "stages_ms": {info64[i]["name"]: round(float(m64[i]), 4) for i in range(len(info64))},
                 "roofline": roofline_of(info64, m64, _measured_peaks()),
-                "interaction_fp64_frac": interaction_fp64_frac(info64, m64)}
+                "interaction_fp64_frac": interaction_fp64_frac(info64, m64),
+                "backward_ms": backward_ms}
 
     if rank != 0:
         return 0

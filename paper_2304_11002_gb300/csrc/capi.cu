@@ -93,14 +93,14 @@ struct octo_fmm {
   int *d_interior = nullptr, *d_leaf = nullptr, *d_boundary = nullptr;
   int *d_st_parity = nullptr, *d_st_root = nullptr, *d_st_near = nullptr;
   Kappa* d_kappa = nullptr;
-  // cross-level pairs: tabulated point-mass pairs (forward), the general remainder
-  // (forward) and the complete lists (adjoint, uploaded on first use)
+  // cross-level pairs: tabulated point-mass pairs and the general remainder (both
+  // directions of every pair, so the adjoint gathers over the same lists)
   int64_t *d_xc_t = nullptr, *d_xc_off = nullptr, *d_xc_ent = nullptr;
   double* d_xc_tab = nullptr;
   int* d_xc_counter = nullptr;
   CrossCells xc{};
   int xc_grid = 0;
-  CrossSet xg, xb;
+  CrossSet xg;
   // batched interaction phase: strategy (MODE_*), persistent work queue and counter
   int mode = 0, requested_mode = 0;
   int min_blocks = 1, n_sm = 0;
@@ -177,9 +177,9 @@ void free_all(octo_fmm* h) {
                   h->d_kappa32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (CrossSet* cs : {&h->xg, &h->xb})
-    for (int64_t* p : {cs->d_ft, cs->d_fs, cs->d_fm, cs->d_fsrc, cs->d_lt, cs->d_ls, cs->d_lm, cs->d_lsrc})
-      if (p) cudaFree(p);
+  for (int64_t* p : {h->xg.d_ft, h->xg.d_fs, h->xg.d_fm, h->xg.d_fsrc, h->xg.d_lt, h->xg.d_ls, h->xg.d_lm,
+                     h->xg.d_lsrc})
+    if (p) cudaFree(p);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto& ev : h->ev)
@@ -441,11 +441,95 @@ std::vector<Kappa> make_kappa(int R) {
 
 namespace {
 
+// Work of the persistent queue's items, in any common unit: per M2L pair of an
+// interior item, per leaf node for the far-field item and for the near item.
+struct ItemCosts {
+  double interior_pair, leaf_far, leaf_near;
+};
+
+// Estimates before measurement, in SM cycles: an M2L pair with correction ~240
+// float32 instructions at 128 per cycle; a leaf node's far field ~1200 entries x 512
+// cells at ~24 instructions per pair (halo staging and boundary pairs included); its
+// near field 170 x 512 pairs of 4 DFMA at 2 per cycle, at about 60 % of that rate
+// when it shares the SM.
+ItemCosts default_costs(const Plan& P) {
+  return {240.0 / 128.0, 512.0 * P.n_st * 24.0 / 128.0, 512.0 * (double)P.st_near.size() * 4.0 / 2.0 * 0.6};
+}
+
+// The persistent work queue (item = (node << 3) | (kind << 1) | half).  Interior
+// items (kind 0, one per half) of the root first (the largest), then of the other
+// levels; leaf items (kind 1, whole node) with refined neighbours before the
+// others.  Float64: all interior items, then all leaf items.  Mixed precision: the
+// float32-bound items (interior, leaf far field) and the float64-bound near items
+// (kind 2) are merged so that every prefix of the queue holds the same fraction of
+// the work of both, so that the two pipes of every SM stay busy side by side.
+std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c) {
+  std::vector<int32_t> q32, q64, q;
+  std::vector<double> w32, w64;
+  auto item = [](int node, int kind, int half) { return (node << 3) | (kind << 1) | half; };
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k : P.interior_nodes)
+      if ((P.level[k] == 0) == (pass == 0))
+        for (int half = 0; half < 2; ++half) {
+          q32.push_back(item(k, 0, half));
+          w32.push_back(256.0 * (P.level[k] == 0 ? (double)P.st_root.size() : (double)P.n_st) * c.interior_pair);
+        }
+  std::vector<char> bnd(P.n_nodes, 0);
+  for (int k : P.boundary_nodes) bnd[k] = 1;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k : P.leaf_nodes)
+      if ((bnd[k] != 0) == (pass == 0)) {
+        q32.push_back(item(k, 1, 0));
+        w32.push_back(c.leaf_far);
+        if (mixed) {
+          q64.push_back(item(k, 2, 0));
+          w64.push_back(c.leaf_near);
+        }
+      }
+  if (!mixed) return q32;
+  double t32 = 0, t64 = 0, c32 = 0, c64 = 0;
+  for (double v : w32) t32 += v;
+  for (double v : w64) t64 += v;
+  size_t i = 0, j = 0;
+  while (i < q32.size() || j < q64.size()) {
+    // take the list whose consumed fraction of its total work is smaller
+    const bool take32 = j == q64.size() || (i < q32.size() && c32 * t64 <= c64 * t32);
+    if (take32) {
+      c32 += w32[i];
+      q.push_back(q32[i++]);
+    } else {
+      c64 += w64[j];
+      q.push_back(q64[j++]);
+    }
+  }
+  return q;
+}
+
+// Mean time (ms) of one launch of the per-kind stage of `kind` (0 if the stage list
+// has none), over three launches on stream ts after a warm-up.
+cudaError_t time_stage(octo_fmm* h, int kind, cudaStream_t ts, cudaEvent_t t0, cudaEvent_t t1, float* ms) {
+  *ms = 0.0f;
+  for (const auto& st : h->stages) {
+    if (st.kind != kind) continue;
+    cudaError_t e = enq_stage(h, st, nullptr, nullptr, nullptr, ts);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, ts);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = enq_stage(h, st, nullptr, nullptr, nullptr, ts);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, ts);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, t0, t1);
+    *ms /= 3.0f;
+    return e;
+  }
+  return cudaSuccess;
+}
+
 // Project autotuner of the batched interaction phase: after one upward pass with
 // this rho, times the interaction stages under each strategy (per-kind launches;
-// persistent queue with the 1- and 2-blocks-per-SM register budgets) on the
-// handle's own tree and keeps the fastest.  Runs once per handle, on the private
-// stream, ordered after the caller's pending work.
+// persistent queue with the 1-, 2- and, in mixed precision, 3-blocks-per-SM register
+// budgets) on the handle's own tree and keeps the fastest.  In mixed precision it
+// first times the three per-kind item stages alone and rebuilds the persistent
+// queue with the measured item costs.  Runs once per handle, on the private stream,
+// ordered after the caller's pending work.
 int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
   cudaStream_t ts = h->cap_stream;
   cudaEvent_t ready = nullptr, t0 = nullptr, t1 = nullptr;
@@ -462,6 +546,23 @@ int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
   } cands[4] = {{MODE_PER_KIND, 1}, {MODE_PERSISTENT, 1}, {MODE_PERSISTENT, 2}, {MODE_PERSISTENT, 3}};
   const int n_cands = h->precision == OCTO_MIXED ? 4 : 3;  // budget 3: mixed precision only
   int best = 0;
+  if (e == cudaSuccess && h->precision == OCTO_MIXED && h->n_items > 0) {
+    // measured item costs -> persistent queue
+    const Plan& P = h->plan;
+    h->mode = MODE_PER_KIND;
+    e = rebuild_stages(h);
+    float t_int = 0, t_far = 0, t_near = 0;
+    if (e == cudaSuccess) e = time_stage(h, S_M2L, ts, t0, t1, &t_int);
+    if (e == cudaSuccess) e = time_stage(h, S_CONV, ts, t0, t1, &t_far);
+    if (e == cudaSuccess) e = time_stage(h, S_NEAR, ts, t0, t1, &t_near);
+    if (e == cudaSuccess && t_int > 0 && t_far > 0 && t_near > 0 && P.kernel_pairs[0] > 0 && P.n_leaf > 0) {
+      const ItemCosts c = {t_int / (double)P.kernel_pairs[0], t_far / (double)P.n_leaf, t_near / (double)P.n_leaf};
+      const std::vector<int32_t> q = build_queue(P, true, c);
+      if ((int)q.size() == h->n_items)
+        e = cudaMemcpyAsync(h->d_queue, q.data(), sizeof(int32_t) * q.size(), cudaMemcpyHostToDevice, ts);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+    }
+  }
   for (int c = 0; c < n_cands && e == cudaSuccess; ++c) {
     h->mode = cands[c].mode;
     h->min_blocks = cands[c].minb;
@@ -624,58 +725,10 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     delete h;
     return create_fail(OCTO_ECUDA, m);
   }
-  // persistent work queue (item = (node << 3) | (kind << 1) | half).  Interior items
-  // (kind 0, one per half) of the root first (the largest), then of the other
-  // levels; leaf items (kind 1, whole node) with refined neighbours before the
-  // others.  Float64: all interior items, then all leaf items.  Mixed precision:
-  // the float32-bound items (interior, leaf far field) and the float64-bound near
-  // items (kind 2) are merged so that every prefix of the queue holds the same
-  // fraction of the estimated work of both (SM cycles: an M2L pair ~240 float32
-  // instructions at 128 per cycle, a far pair ~7, a near pair 4 DFMA at 2 per
-  // cycle), so that the two pipes of every SM stay busy side by side.
+  // persistent work queue (see build_queue); mixed precision: estimated item costs
+  // until the autotuner has measured them
   {
-    std::vector<int32_t> q32, q64, q;
-    std::vector<double> w32, w64;
-    const double n_far = (double)P.n_st, n_near = (double)P.st_near.size();
-    auto item = [](int node, int kind, int half) { return (node << 3) | (kind << 1) | half; };
-    for (int pass = 0; pass < 2; ++pass)
-      for (int k : P.interior_nodes)
-        if ((P.level[k] == 0) == (pass == 0))
-          for (int half = 0; half < 2; ++half) {
-            q32.push_back(item(k, 0, half));
-            w32.push_back(256.0 * (P.level[k] == 0 ? (double)P.st_root.size() : n_far) * 240.0 / 128.0);
-          }
-    std::vector<char> bnd(P.n_nodes, 0);
-    for (int k : P.boundary_nodes) bnd[k] = 1;
-    for (int pass = 0; pass < 2; ++pass)
-      for (int k : P.leaf_nodes)
-        if ((bnd[k] != 0) == (pass == 0)) {
-          q32.push_back(item(k, 1, 0));
-          w32.push_back(512.0 * n_far * 7.0 / 128.0);
-          if (precision == OCTO_MIXED) {
-            q64.push_back(item(k, 2, 0));
-            w64.push_back(512.0 * n_near * 4.0 / 2.0);
-          }
-        }
-    if (precision == OCTO_MIXED) {
-      double t32 = 0, t64 = 0, c32 = 0, c64 = 0;
-      for (double v : w32) t32 += v;
-      for (double v : w64) t64 += v;
-      size_t i = 0, j = 0;
-      while (i < q32.size() || j < q64.size()) {
-        // take the list whose consumed fraction of its total work is smaller
-        const bool take32 = j == q64.size() || (i < q32.size() && c32 * t64 <= c64 * t32);
-        if (take32) {
-          c32 += w32[i];
-          q.push_back(q32[i++]);
-        } else {
-          c64 += w64[j];
-          q.push_back(q64[j++]);
-        }
-      }
-    } else {
-      q = q32;
-    }
+    const std::vector<int32_t> q = build_queue(P, precision == OCTO_MIXED, default_costs(P));
     h->n_items = (int)q.size();
     e = upload(&h->d_queue, q);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_counter, sizeof(int));
@@ -802,8 +855,6 @@ int octo_fmm_backward(octo_fmm_t h, const double* dphi, const double* dg, double
     general.insert(general.end(), P.boundary_nodes.begin(), P.boundary_nodes.end());
     h->n_general = (int)general.size();
     e = upload(&h->d_general, general);
-    // the adjoint walks the complete cross-level lists
-    if (e == cudaSuccess) e = upload_cross(P, P.x_targets, P.x_start, P.x_mid, P.x_sources, h->xb);
     // the adjoint kernels keep large per-thread frames: make sure the stack limit covers them
     size_t need = 0, cur = 0;
     if (e == cudaSuccess) e = adjoint_local_bytes(&need);
@@ -834,8 +885,10 @@ int octo_fmm_backward(octo_fmm_t h, const double* dphi, const double* dg, double
   ba.level_start = P.level_start.data();
   ba.max_level = P.max_level;
   ba.st = h->st;
-  ba.xf = h->xb.f;
-  ba.xl = h->xb.l;
+  ba.xf = h->xg.f;  // the same cross-level lists as the forward (both directions of every pair)
+  ba.xl = h->xg.l;
+  ba.xc = h->xc;
+  ba.xc_grid = h->xc_grid;
   ba.err = h->d_err;
   e = launch_backward(h->dt, ba, (cudaStream_t)stream);
   return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "backward");

@@ -106,6 +106,10 @@ cudaError_t launch_cross_list(const DevTree& t, const CrossList& xl, bool full, 
 // Tabulated point-mass pairs, float64 in both precision modes.  grid: a multiple of
 // the SM count (cross_cells_blocks_per_sm gives the resident blocks per SM).
 cudaError_t cross_cells_blocks_per_sm(const CrossCells& xc, int* blocks);
+// Adjoint of the tabulated pairs: mpb (mass part) of every list target from the
+// local-expansion adjoints locb of its partners.
+cudaError_t launch_cross_cells_adjoint(const DevTree& t, const CrossCells& xc, const double* locb, double* mpb,
+                                       int grid, cudaStream_t s);
 cudaError_t launch_cross_cells(const DevTree& t, const CrossCells& xc, const double* mp, double* loc, int grid,
                                cudaStream_t s);
 
@@ -126,7 +130,9 @@ struct BackwardArgs {
   const int* level_start;    // host array [max_level + 2]
   int max_level;
   Stencils st;
-  CrossList xf, xl;
+  CrossList xf, xl;          // general cross-level pairs (refined targets, leaf targets)
+  CrossCells xc;             // tabulated cross-level pairs of leaf cells one level apart
+  int xc_grid;
   int* err;                  // device word: bits of failed index checks (see kernels_adjoint.cu)
 };
 cudaError_t launch_backward(const DevTree& t, const BackwardArgs& ba, cudaStream_t s);

@@ -562,6 +562,8 @@ cudaError_t launch_backward(const DevTree& t, const BackwardArgs& ba, cudaStream
   if (ba.n_general) k_adj_general<<<4 * ba.n_general, 128, 0, s>>>(t, ba.general_nodes, ba.st, as);
   if (ba.xf.n_targets) k_adj_cross<true><<<(ba.xf.n_targets + 127) / 128, 128, 0, s>>>(t, ba.xf, as);
   if (ba.xl.n_targets) k_adj_cross<false><<<(ba.xl.n_targets + 127) / 128, 128, 0, s>>>(t, ba.xl, as);
+  e = launch_cross_cells_adjoint(t, ba.xc, ba.locb, ba.mpb, ba.xc_grid, s);
+  if (e != cudaSuccess) return e;
   for (int l = 0; l < ba.max_level; ++l) {
     const int n = ba.level_start[l + 1] - ba.level_start[l];
     if (n > 0) k_adj_m2m<<<2 * n, 256, 0, s>>>(t, ba.level_start[l], as);

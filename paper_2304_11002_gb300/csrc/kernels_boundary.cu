@@ -88,6 +88,54 @@ __global__ void __launch_bounds__(kCrossCellsThreads) k_cross_cells(DevTree t, C
   }
 }
 
+// Adjoint of k_cross_cells (gather form).  Both directions of every pair are in
+// the list, so the partners Y of list target X are the cells X was a source for.
+// With fixed leaf centres only X's mass matters:
+//   d S / d m_X = sum_Y [ -Lb0_Y / |R| + Lb1_Y . (x_Y - x_X) / |R|^3 ],
+// and in the table's units (v = c_X - c_Y, row of the entry X <- Y, h = h_X)
+//   1 / |R| = row0 / h,   (x_Y - x_X)_k / |R|^3 = -sign(v_k) row_k / h^2.
+__global__ void __launch_bounds__(kCrossCellsThreads) k_cross_cells_adjoint(DevTree t, CrossCells xc,
+                                                                            const double* __restrict__ locb,
+                                                                            double* __restrict__ mpb) {
+  extern __shared__ double2 tab2[];
+  const double2* __restrict__ gt = reinterpret_cast<const double2*>(xc.table);
+  for (int i = threadIdx.x; i < 2 * xc.n_rows; i += blockDim.x) tab2[i] = gt[i];
+  __syncthreads();
+  const int64_t NC = t.NC;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int s = 0;
+    if (lane == 0) s = atomicAdd(xc.counter, 1);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (s >= xc.n_slices) return;
+    const int64_t o0 = xc.slice_off[s];
+    const int64_t width = (xc.slice_off[s + 1] - o0) >> 5;
+    const int64_t* __restrict__ ent = xc.entries + o0 + lane;
+    double S0 = 0.0, S1 = 0.0;
+    for (int64_t k = 0; k < width; k += 2) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int64_t e = __ldcs(ent + 32 * (k + u));
+        const int64_t y = e >> 20;
+        const int row = (int)(e & 0xffff);
+        const double2 a = tab2[2 * row], b = tab2[2 * row + 1];
+        const double b0 = __ldg(locb + G_L0 * NC + y);
+        const double bx = __ldg(locb + (G_L1 + 0) * NC + y), by = __ldg(locb + (G_L1 + 1) * NC + y),
+                     bz = __ldg(locb + (G_L1 + 2) * NC + y);
+        S0 = fma(b0, a.x, S0);
+        S1 = fma(flip_sign(bx, (e >> 16) & 1), a.y, S1);
+        S1 = fma(flip_sign(by, (e >> 17) & 1), b.x, S1);
+        S1 = fma(flip_sign(bz, (e >> 18) & 1), b.y, S1);
+      }
+    }
+    const int64_t X = xc.targets[(int64_t)s * 32 + lane];
+    if (X >= 0) {
+      const double ih = 1.0 / t.h[t.level[X >> 9]];
+      mpb[X] -= S0 * ih + S1 * ih * ih;
+    }
+  }
+}
+
 template <bool FULL, bool MIXED>
 __global__ void __launch_bounds__(128) k_cross_w(DevTree t, CrossList xl, const double* __restrict__ mp,
                                                  double* __restrict__ loc) {
@@ -199,6 +247,17 @@ cudaError_t launch_cross_cells(const DevTree& t, const CrossCells& xc, const dou
   cudaError_t e = cudaMemsetAsync(xc.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_cross_cells<<<grid, kCrossCellsThreads, smem, s>>>(t, xc, mp, loc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cross_cells_adjoint(const DevTree& t, const CrossCells& xc, const double* locb, double* mpb,
+                                       int grid, cudaStream_t s) {
+  if (xc.n_slices == 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * 4 * (size_t)xc.n_rows;
+  cudaError_t e = cudaFuncSetAttribute(k_cross_cells_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaMemsetAsync(xc.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_cross_cells_adjoint<<<grid, kCrossCellsThreads, smem, s>>>(t, xc, locb, mpb);
   return cudaGetLastError();
 }
 
