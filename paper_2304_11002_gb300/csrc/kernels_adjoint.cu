@@ -8,6 +8,7 @@
 // result is deterministic.  Adjoint state: mpb [20][NC] (multipole adjoints, packed
 // like the multipoles) and locb [23][NC] (local-expansion adjoints).
 #include "kernels.h"
+#include "pair_vjp.cuh"
 #include "sym.cuh"
 
 namespace octo {
@@ -29,85 +30,6 @@ __device__ __forceinline__ void unpack_a(int e, int& dx, int& dy, int& dz) {
   dx = (int)(int8_t)(e & 0xff);
   dy = (int)(int8_t)((e >> 8) & 0xff);
   dz = (int)(int8_t)((e >> 16) & 0xff);
-}
-
-// Gradients of S = Lb . (contribution of source S to target T) for one M2L pair
-// with R = X_T - X_S (see m2l_pair for the forward expression).  Lb: L0, L1(3),
-// L2(6), L3(10), dg(3) adjoints of the target; LFULL: the target carries L2/L3.
-struct PairGrad {
-  double R[3];   // dS/dR
-  double m;      // dS/d m_source
-  double Q[6];   // dS/d Q_source (packed)
-  double O[10];  // dS/d O_source (packed)
-  double Oh[10]; // dS/d (O_target / m_target) (packed)
-};
-
-template <bool LFULL>
-__device__ __forceinline__ void pair_grad(double x, double y, double z, double mS, const double* Q, const double* O,
-                                          const double* Oh, const double* Lb, PairGrad& g) {
-  double D[sym::kNComp];
-  sym::derivatives(x, y, z, D);
-  const double* dgb = Lb + 20;
-  double E4[10];  // sum_a dgb_a D4[(q3) + a]
-#pragma unroll
-  for (int q = 0; q < 10; ++q) {
-    double s = 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) s += dgb[a] * D[sym::up(10 + q, a)];
-    E4[q] = s;
-  }
-  // adjoints of the derivative tensors D^(0..4)
-  double T[35];
-  T[0] = -mS * Lb[0];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) T[1 + a] = -mS * Lb[1 + a];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) T[4 + q] = -0.5 * Lb[0] * Q[q] * sym::mult(4 + q) - (LFULL ? mS * Lb[4 + q] : 0.0);
-#pragma unroll
-  for (int q = 0; q < 10; ++q) T[10 + q] = Lb[0] * sym::mult(10 + q) * O[q] * (1.0 / 6.0) - (LFULL ? mS * Lb[10 + q] : 0.0);
-#pragma unroll
-  for (int q = 20; q < 35; ++q) T[q] = 0.0;
-#pragma unroll
-  for (int q = 0; q < 6; ++q)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) T[sym::up(4 + q, a)] -= 0.5 * Lb[1 + a] * sym::mult(4 + q) * Q[q];
-#pragma unroll
-  for (int q = 0; q < 10; ++q) {
-    const double C = mS * Oh[q] - O[q];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) T[sym::up(10 + q, a)] += dgb[a] * sym::mult(10 + q) * C * (1.0 / 6.0);
-  }
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < 35; ++q) s += T[q] * D[sym::up(q, f)];
-    g.R[f] = s;
-  }
-  double gm = -Lb[0] * D[0];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) gm -= Lb[1 + a] * D[1 + a];
-  if (LFULL) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) gm -= Lb[4 + q] * D[4 + q];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) gm -= Lb[10 + q] * D[10 + q];
-  }
-#pragma unroll
-  for (int q = 0; q < 10; ++q) gm += sym::mult(10 + q) * Oh[q] * E4[q] * (1.0 / 6.0);
-  g.m = gm;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    double s = Lb[0] * D[4 + q];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) s += Lb[1 + a] * D[sym::up(4 + q, a)];
-    g.Q[q] = -0.5 * sym::mult(4 + q) * s;
-  }
-#pragma unroll
-  for (int q = 0; q < 10; ++q) {
-    g.O[q] = sym::mult(10 + q) * (1.0 / 6.0) * (Lb[0] * D[10 + q] - E4[q]);
-    g.Oh[q] = mS * sym::mult(10 + q) * (1.0 / 6.0) * E4[q];
-  }
 }
 
 struct AdjState {
@@ -298,10 +220,39 @@ __global__ void __launch_bounds__(256) k_adj_conv(DevTree t, const int* __restri
 }
 
 // ------------------------------------------------------------ general same-level pairs^T
+// Visits the stencil partners Y of cell (a, b, c) of `node` that form a general
+// pair with it (not both leaves) and calls f(Y, yleaf).
+template <typename F>
+__device__ __forceinline__ void general_partners(const DevTree& t, const Stencils& st, int node, int lvl, int p,
+                                                 int a, int b, int c, bool xleaf, int* err, F&& f) {
+  const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
+  const int ntab = lvl == 0 ? st.n_root : st.n_st;
+  const int* nb = t.nbr + 27 * node;
+  for (int s = 0; s < ntab; ++s) {
+    int dx, dy, dz;
+    unpack_a(__ldg(tab + s), dx, dy, dz);
+    const int sa = a + dx, sb = b + dy, sc = c + dz;
+    if (!(sa >= -8 && sa < 16 && sb >= -8 && sb < 16 && sc >= -8 && sc < 16)) {
+      atomicOr(err, 8);
+      continue;
+    }
+    const int sn = __ldg(nb + ((sa >> 3) + 1) + 3 * ((sb >> 3) + 1) + 9 * ((sc >> 3) + 1));
+    if (sn >= t.n_nodes) {
+      atomicOr(err, 8);
+      continue;
+    }
+    if (sn < 0) continue;
+    const bool yleaf = __ldg(t.children + 8 * sn) < 0;
+    if (xleaf && yleaf) continue;  // leaf-leaf pairs: k_adj_conv
+    f((int64_t)sn * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7), yleaf);
+  }
+}
+
 // Cell X of an interior node: every stencil partner Y; cell X of a leaf node: the
-// partners in refined neighbour nodes.  (a) X as target of (X <- Y): gradients for
-// X's centre and octupole; (b) X as source of (Y <- X): gradients for X's centre,
-// mass and moments.  Leaf cells keep only the mass gradient.
+// partners in refined neighbour nodes.  Two passes over the partners keep the live
+// state small: (a) X as target of (X <- Y) gives the gradients for X's centre and
+// octupole (through Oh = O / m); (b) X as source of (Y <- X) gives those for X's
+// centre, mass and moments.  Leaf cells keep only the mass gradient.
 __global__ void __launch_bounds__(128) k_adj_general(DevTree t, const int* __restrict__ nodes, Stencils st,
                                                      AdjState as) {
   const int node = nodes[blockIdx.x >> 2];
@@ -316,62 +267,65 @@ __global__ void __launch_bounds__(128) k_adj_general(DevTree t, const int* __res
   const double* mp = as.mp;
   const double mX = mp[X];
   const double XX0 = mp[(F_X + 0) * NC + X], XX1 = mp[(F_X + 1) * NC + X], XX2 = mp[(F_X + 2) * NC + X];
-  double QX[6], OX[10], OhX[10], LbX[23];
-  for (int i = 0; i < 6; ++i) QX[i] = mp[(F_Q + i) * NC + X];
-  for (int i = 0; i < 10; ++i) OX[i] = mp[(F_O + i) * NC + X], OhX[i] = xleaf ? 0.0 : OX[i] / mX;
-  if (!xleaf) load_lb(as.locb, NC, X, true, LbX);
-  double gX[3] = {0, 0, 0}, gm = 0, gQ[6] = {0, 0, 0, 0, 0, 0}, gO[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double gOh[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
-  const int ntab = lvl == 0 ? st.n_root : st.n_st;
-  const int* nb = t.nbr + 27 * node;
-  for (int s = 0; s < ntab; ++s) {
-    int dx, dy, dz;
-    unpack_a(__ldg(tab + s), dx, dy, dz);
-    const int sa = a + dx, sb = b + dy, sc = c + dz;
-    const int sn = __ldg(nb + ((sa >> 3) + 1) + 3 * ((sb >> 3) + 1) + 9 * ((sc >> 3) + 1));
-    ADJ_SKIP_UNLESS(sa >= -8 && sa < 16 && sb >= -8 && sb < 16 && sc >= -8 && sc < 16 && sn < t.n_nodes, 8);
-    if (sn < 0) continue;
-    const bool yleaf = __ldg(t.children + 8 * sn) < 0;
-    if (xleaf && yleaf) continue;  // leaf-leaf pairs: k_adj_conv
-    const int64_t Y = (int64_t)sn * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
-    const double mY = mp[Y];
-    const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
-    double QY[6], OY[10], OhY[10], LbY[23];
-    for (int i = 0; i < 6; ++i) QY[i] = mp[(F_Q + i) * NC + Y];
-    for (int i = 0; i < 10; ++i) OY[i] = mp[(F_O + i) * NC + Y], OhY[i] = yleaf ? 0.0 : OY[i] / mY;
-    PairGrad g;
-    if (!xleaf) {  // (a) X <- Y
-      pair_grad<true>(R0, R1, R2, mY, QY, OY, OhX, LbX, g);
+  double gX[3] = {0, 0, 0}, gm = 0;
+  if (!xleaf) {  // (a) X <- Y
+    const double inv_m = 1.0 / mX;
+    double OhX[10], LbX[23], gOh[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 10; ++i) OhX[i] = mp[(F_O + i) * NC + X] * inv_m;
+    load_lb(as.locb, NC, X, true, LbX);
+    general_partners(t, st, node, lvl, p, a, b, c, false, err, [&](int64_t Y, bool) {
+      double QY[6], OY[10];
+      const double mY = mp[Y];
+      const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
+      for (int i = 0; i < 6; ++i) QY[i] = mp[(F_Q + i) * NC + Y];
+      for (int i = 0; i < 10; ++i) OY[i] = mp[(F_O + i) * NC + Y];
+      PairVJP g;
+      m2l_pair_vjp<true, true, false, true>(R0, R1, R2, mY, QY, OY, OhX, LbX, g);
       for (int f = 0; f < 3; ++f) gX[f] += g.R[f];
       for (int i = 0; i < 10; ++i) gOh[i] += g.Oh[i];
-    }
-    // (b) Y <- X, R_YX = -R
-    load_lb(as.locb, NC, Y, !yleaf, LbY);
-    if (yleaf)
-      pair_grad<false>(-R0, -R1, -R2, mX, QX, OX, OhY, LbY, g);
-    else
-      pair_grad<true>(-R0, -R1, -R2, mX, QX, OX, OhY, LbY, g);
-    for (int f = 0; f < 3; ++f) gX[f] -= g.R[f];
-    gm += g.m;
-    for (int i = 0; i < 6; ++i) gQ[i] += g.Q[i];
-    for (int i = 0; i < 10; ++i) gO[i] += g.O[i];
-  }
-  if (!xleaf) {  // Oh = O / m
+    });
+    // Oh = O * (1 / m)
     for (int i = 0; i < 10; ++i) {
-      gO[i] += gOh[i] / mX;
-      gm -= gOh[i] * OX[i] / (mX * mX);
+      as.mpb[(F_O + i) * NC + X] += gOh[i] * inv_m;
+      gm -= gOh[i] * OhX[i] * inv_m;
     }
-    for (int f = 0; f < 3; ++f) as.mpb[(F_X + f) * NC + X] += gX[f];
-    for (int i = 0; i < 6; ++i) as.mpb[(F_Q + i) * NC + X] += gQ[i];
-    for (int i = 0; i < 10; ++i) as.mpb[(F_O + i) * NC + X] += gO[i];
+  }
+  {  // (b) Y <- X, R_YX = -R
+    double QX[6], OX[10], gQ[6] = {0, 0, 0, 0, 0, 0}, gO[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 6; ++i) QX[i] = mp[(F_Q + i) * NC + X];
+    for (int i = 0; i < 10; ++i) OX[i] = mp[(F_O + i) * NC + X];
+    general_partners(t, st, node, lvl, p, a, b, c, xleaf, err, [&](int64_t Y, bool yleaf) {
+      const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
+      double LbY[23];
+      PairVJP g;
+      if (yleaf) {
+        load_lb(as.locb, NC, Y, false, LbY);
+        m2l_pair_vjp<false, false, true, false>(-R0, -R1, -R2, mX, QX, OX, nullptr, LbY, g);
+      } else {
+        double OhY[10];
+        const double inv_mY = 1.0 / mp[Y];
+        for (int i = 0; i < 10; ++i) OhY[i] = mp[(F_O + i) * NC + Y] * inv_mY;
+        load_lb(as.locb, NC, Y, true, LbY);
+        m2l_pair_vjp<true, true, true, false>(-R0, -R1, -R2, mX, QX, OX, OhY, LbY, g);
+      }
+      for (int f = 0; f < 3; ++f) gX[f] -= g.R[f];
+      gm += g.m;
+      for (int i = 0; i < 6; ++i) gQ[i] += g.Q[i];
+      for (int i = 0; i < 10; ++i) gO[i] += g.O[i];
+    });
+    if (!xleaf) {
+      for (int f = 0; f < 3; ++f) as.mpb[(F_X + f) * NC + X] += gX[f];
+      for (int i = 0; i < 6; ++i) as.mpb[(F_Q + i) * NC + X] += gQ[i];
+      for (int i = 0; i < 10; ++i) as.mpb[(F_O + i) * NC + X] += gO[i];
+    }
   }
   as.mpb[X] += gm;
 }
 
 // ------------------------------------------------------------ cross-level pairs^T
 // The cross-level lists hold both directions of every pair, so the partners of a
-// cell as target are also its partners as source.
+// cell as target are also its partners as source.  Same two passes as the general
+// pairs; (a) only where X carries L2/L3 and an octupole (FULL).
 template <bool FULL>
 __global__ void __launch_bounds__(128) k_adj_cross(DevTree t, CrossList xl, AdjState as) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -383,47 +337,62 @@ __global__ void __launch_bounds__(128) k_adj_cross(DevTree t, CrossList xl, AdjS
   ADJ_RETURN_UNLESS(X >= 0 && X < NC, 16);
   const double mX = mp[X];
   const double XX0 = mp[(F_X + 0) * NC + X], XX1 = mp[(F_X + 1) * NC + X], XX2 = mp[(F_X + 2) * NC + X];
-  double QX[6], OX[10], OhX[10], LbX[23];
-  for (int k = 0; k < 6; ++k) QX[k] = mp[(F_Q + k) * NC + X];
-  for (int k = 0; k < 10; ++k) OX[k] = mp[(F_O + k) * NC + X], OhX[k] = FULL ? OX[k] / mX : 0.0;
-  load_lb(as.locb, NC, X, FULL, LbX);
-  double gX[3] = {0, 0, 0}, gm = 0, gQ[6] = {0, 0, 0, 0, 0, 0}, gO[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double gOh[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int64_t e = xl.start[i]; e < xl.start[i + 1]; ++e) {
-    const int64_t Y = xl.sources[e];
-    ADJ_SKIP_UNLESS(Y >= 0 && Y < NC, 16);
-    const bool yleaf = t.children[8 * (Y / 512)] < 0;
-    const double mY = mp[Y];
-    const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
-    double QY[6], OY[10], OhY[10], LbY[23];
-    for (int k = 0; k < 6; ++k) QY[k] = mp[(F_Q + k) * NC + Y];
-    for (int k = 0; k < 10; ++k) OY[k] = mp[(F_O + k) * NC + Y], OhY[k] = yleaf ? 0.0 : OY[k] / mY;
-    PairGrad g;
-    // (a) X <- Y (only X's centre and octupole matter; both are constants for leaves)
-    if (FULL) {
-      pair_grad<true>(R0, R1, R2, mY, QY, OY, OhX, LbX, g);
+  const int64_t e0 = xl.start[i], e1 = xl.start[i + 1];
+  double gX[3] = {0, 0, 0}, gm = 0;
+  if constexpr (FULL) {  // (a) X <- Y
+    const double inv_m = 1.0 / mX;
+    double OhX[10], LbX[23], gOh[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 10; ++k) OhX[k] = mp[(F_O + k) * NC + X] * inv_m;
+    load_lb(as.locb, NC, X, true, LbX);
+    for (int64_t e = e0; e < e1; ++e) {
+      const int64_t Y = xl.sources[e];
+      ADJ_SKIP_UNLESS(Y >= 0 && Y < NC, 16);
+      double QY[6], OY[10];
+      const double mY = mp[Y];
+      const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
+      for (int k = 0; k < 6; ++k) QY[k] = mp[(F_Q + k) * NC + Y];
+      for (int k = 0; k < 10; ++k) OY[k] = mp[(F_O + k) * NC + Y];
+      PairVJP g;
+      m2l_pair_vjp<true, true, false, true>(R0, R1, R2, mY, QY, OY, OhX, LbX, g);
       for (int f = 0; f < 3; ++f) gX[f] += g.R[f];
       for (int k = 0; k < 10; ++k) gOh[k] += g.Oh[k];
     }
-    // (b) Y <- X
-    load_lb(as.locb, NC, Y, !yleaf, LbY);
-    if (yleaf)
-      pair_grad<false>(-R0, -R1, -R2, mX, QX, OX, OhY, LbY, g);
-    else
-      pair_grad<true>(-R0, -R1, -R2, mX, QX, OX, OhY, LbY, g);
-    for (int f = 0; f < 3; ++f) gX[f] -= g.R[f];
-    gm += g.m;
-    for (int k = 0; k < 6; ++k) gQ[k] += g.Q[k];
-    for (int k = 0; k < 10; ++k) gO[k] += g.O[k];
-  }
-  if (FULL) {
     for (int k = 0; k < 10; ++k) {
-      gO[k] += gOh[k] / mX;
-      gm -= gOh[k] * OX[k] / (mX * mX);
+      as.mpb[(F_O + k) * NC + X] += gOh[k] * inv_m;
+      gm -= gOh[k] * OhX[k] * inv_m;
     }
-    for (int f = 0; f < 3; ++f) as.mpb[(F_X + f) * NC + X] += gX[f];
-    for (int k = 0; k < 6; ++k) as.mpb[(F_Q + k) * NC + X] += gQ[k];
-    for (int k = 0; k < 10; ++k) as.mpb[(F_O + k) * NC + X] += gO[k];
+  }
+  {  // (b) Y <- X
+    double QX[6], OX[10], gQ[6] = {0, 0, 0, 0, 0, 0}, gO[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 6; ++k) QX[k] = mp[(F_Q + k) * NC + X];
+    for (int k = 0; k < 10; ++k) OX[k] = mp[(F_O + k) * NC + X];
+    for (int64_t e = e0; e < e1; ++e) {
+      const int64_t Y = xl.sources[e];
+      ADJ_SKIP_UNLESS(Y >= 0 && Y < NC, 16);
+      const bool yleaf = t.children[8 * (Y / 512)] < 0;
+      const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
+      double LbY[23];
+      PairVJP g;
+      if (yleaf) {
+        load_lb(as.locb, NC, Y, false, LbY);
+        m2l_pair_vjp<false, false, true, false>(-R0, -R1, -R2, mX, QX, OX, nullptr, LbY, g);
+      } else {
+        double OhY[10];
+        const double inv_mY = 1.0 / mp[Y];
+        for (int k = 0; k < 10; ++k) OhY[k] = mp[(F_O + k) * NC + Y] * inv_mY;
+        load_lb(as.locb, NC, Y, true, LbY);
+        m2l_pair_vjp<true, true, true, false>(-R0, -R1, -R2, mX, QX, OX, OhY, LbY, g);
+      }
+      for (int f = 0; f < 3; ++f) gX[f] -= g.R[f];
+      gm += g.m;
+      for (int k = 0; k < 6; ++k) gQ[k] += g.Q[k];
+      for (int k = 0; k < 10; ++k) gO[k] += g.O[k];
+    }
+    if (FULL) {
+      for (int f = 0; f < 3; ++f) as.mpb[(F_X + f) * NC + X] += gX[f];
+      for (int k = 0; k < 6; ++k) as.mpb[(F_Q + k) * NC + X] += gQ[k];
+      for (int k = 0; k < 10; ++k) as.mpb[(F_O + k) * NC + X] += gO[k];
+    }
   }
   as.mpb[X] += gm;
 }
