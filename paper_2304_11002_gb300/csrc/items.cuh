@@ -86,22 +86,39 @@ __device__ __forceinline__ void interior_f64(const DevTree& t, int node, int hal
 // Positions relative to node centres in cell widths: R = x_A - (x_B + 8 o) for a
 // source in neighbour slot o.  Accumulation: the pair terms of kAccBlock stencil
 // entries are summed in plain float32 (fused multiply-adds); each partial sum then
-// gets its deferred Kronecker parts (acc_finish is linear) and is added into the
-// target's float64 local expansion in global memory, which stays in L2 and is
-// touched once per block of entries.  A partial holds few terms, so its rounding
-// error stays a few float32 ulps of the partial, and the float64 sums add no error
-// of their own: the accuracy of a compensated float32 sum at about a fifth of the
-// instructions, with no accumulator registers beyond the 27 partials and no shared
-// memory (which is left to L1, where the source records are cached).
+// gets its deferred Kronecker parts (acc_finish is linear) and is added by an
+// error-free transformation (TwoSum) into a float32 (sum, compensation) pair per
+// field, kept in shared memory; sum + compensation is converted to float64 once, at
+// the end.  A partial holds few terms, so its rounding error stays a few float32
+// ulps of the partial, and the pairs add only the compensation's own rounding (a
+// float32 ulp of an already float32-ulp-sized error): the accuracy of a compensated
+// float32 sum at about a fifth of the instructions, with no float64 arithmetic
+// inside the loop (the float64 pipe stays free for the near-field items that share
+// the SM) and the 27 partials as the only accumulator registers.
 constexpr int kAccBlock = 32;
+constexpr int kInteriorFields = N_LOC;
 
-__device__ __forceinline__ void flush_partial(Acc<float>& a, double* __restrict__ loc, int64_t NC, int64_t tgt) {
+// Shared memory of an interior item: one float2 (sum, compensation) per field and
+// thread, field-major ([field][thread]), so that a warp's accesses are contiguous.
+__host__ __device__ constexpr size_t interior_smem_bytes() { return sizeof(float2) * kInteriorFields * kThreads; }
+
+// s + c <- s + c + p with the rounding error of s + p kept exactly in c's update
+// (Knuth's TwoSum: six float32 additions, no branch, valid for any magnitudes).
+__device__ __forceinline__ void two_sum_into(float2& sc, float p) {
+  const float s = sc.x + p;
+  const float bp = s - sc.x;
+  const float err = (sc.x - (s - bp)) + (p - bp);
+  sc.x = s;
+  sc.y += err;
+}
+
+__device__ __forceinline__ void flush_partial(Acc<float>& a, float2* __restrict__ sc) {
   acc_finish(a);
-  loc[G_L0 * NC + tgt] += a.L0;
-  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] += a.L1[i];
-  for (int i = 0; i < 6; ++i) loc[(G_L2 + i) * NC + tgt] += a.L2[i];
-  for (int i = 0; i < 10; ++i) loc[(G_L3 + i) * NC + tgt] += a.L3[i];
-  for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] += a.dg[i];
+  two_sum_into(sc[G_L0 * kThreads], a.L0);
+  for (int i = 0; i < 3; ++i) two_sum_into(sc[(G_L1 + i) * kThreads], a.L1[i]);
+  for (int i = 0; i < 6; ++i) two_sum_into(sc[(G_L2 + i) * kThreads], a.L2[i]);
+  for (int i = 0; i < 10; ++i) two_sum_into(sc[(G_L3 + i) * kThreads], a.L3[i]);
+  for (int i = 0; i < 3; ++i) two_sum_into(sc[(G_DG + i) * kThreads], a.dg[i]);
   acc_zero(a);
 }
 
@@ -117,7 +134,8 @@ __device__ __forceinline__ void load_mp32(const float* __restrict__ mp32, int64_
 }
 
 __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int half, const Stencils& st,
-                                             const float* __restrict__ mp32, double* __restrict__ loc) {
+                                             const float* __restrict__ mp32, double* __restrict__ loc,
+                                             unsigned char* smem) {
   int p, zh, a, b, c;
   cell_of(half, threadIdx.x, p, zh, a, b, c);
   const int lvl = t.level[node];
@@ -135,7 +153,8 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
   const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
   const int ntab = lvl == 0 ? st.n_root : st.n_st;
   const int* nb = t.nbr + 27 * node;
-  for (int f = 0; f < N_LOC; ++f) loc[f * NC + tgt] = 0.0;
+  float2* sc = reinterpret_cast<float2*>(smem) + threadIdx.x;
+  for (int f = 0; f < kInteriorFields; ++f) sc[f * kThreads] = make_float2(0.0f, 0.0f);
   Acc<float> part;
   acc_zero(part);
   for (int s0 = 0; s0 < ntab; s0 += kAccBlock) {
@@ -156,15 +175,20 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
       const float rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
       m2l_pair<true, true>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, part);
     }
-    flush_partial(part, loc, NC, tgt);
+    flush_partial(part, sc);
   }
-  // unit cell width -> physical units: L_n scales with h^-(n+1), dg with h^-2
+  // sum + compensation in float64; unit cell width -> physical units: L_n scales
+  // with h^-(n+1), dg with h^-2
   const double ih = 1.0 / t.h[lvl], ih2 = ih * ih, ih3 = ih2 * ih, ih4 = ih2 * ih2;
-  loc[G_L0 * NC + tgt] *= ih;
-  for (int i = 0; i < 3; ++i) loc[(G_L1 + i) * NC + tgt] *= ih2;
-  for (int i = 0; i < 6; ++i) loc[(G_L2 + i) * NC + tgt] *= ih3;
-  for (int i = 0; i < 10; ++i) loc[(G_L3 + i) * NC + tgt] *= ih4;
-  for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] *= ih2;
+  auto out = [&](int f, double scale) {
+    const float2 v = sc[f * kThreads];
+    loc[f * NC + tgt] = ((double)v.x + (double)v.y) * scale;
+  };
+  out(G_L0, ih);
+  for (int i = 0; i < 3; ++i) out(G_L1 + i, ih2);
+  for (int i = 0; i < 6; ++i) out(G_L2 + i, ih3);
+  for (int i = 0; i < 10; ++i) out(G_L3 + i, ih4);
+  for (int i = 0; i < 3; ++i) out(G_DG + i, ih2);
 }
 
 // ------------------------------------------------------------ leaf item

@@ -21,9 +21,10 @@ __global__ void __launch_bounds__(items::kThreads, MIXED ? 3 : 1) k_interior_ite
                                                                      Stencils st, const double* __restrict__ mp,
                                                                      const float* __restrict__ mp32,
                                                                      double* __restrict__ loc) {
+  extern __shared__ __align__(16) unsigned char smem[];
   const int node = nodes[blockIdx.x >> 1];
   if (MIXED)
-    items::interior_f32(t, node, blockIdx.x & 1, st, mp32, loc);
+    items::interior_f32(t, node, blockIdx.x & 1, st, mp32, loc, smem);
   else
     items::interior_f64(t, node, blockIdx.x & 1, st, mp, loc);
 }
@@ -67,21 +68,22 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
       items::leaf_item<MIXED>(t, node, st, mp, mp32, loc, smem);
     } else {
       if (MIXED)
-        items::interior_f32(t, node, half, st, mp32, loc);
+        items::interior_f32(t, node, half, st, mp32, loc, smem);
       else
         items::interior_f64(t, node, half, st, mp, loc);
     }
   }
 }
 
-// Resident blocks per SM of a persistent variant (sets its shared-memory limit);
-// called once per handle, outside any stream capture.
-// Dynamic shared memory of the persistent kernel (the interior items use none).
+// Dynamic shared memory of the persistent kernel: the largest of its item kinds
+// (float64 interior items use none).
 size_t persistent_smem_bytes(const Stencils& st, bool mixed) {
   const size_t leaf = items::leaf_smem_bytes(st, mixed);
-  return mixed ? std::max(leaf, items::near_smem_bytes(st)) : leaf;
+  return mixed ? std::max({leaf, items::near_smem_bytes(st), items::interior_smem_bytes()}) : leaf;
 }
 
+// Resident blocks per SM of a persistent variant (sets its shared-memory limit);
+// called once per handle, outside any stream capture.
 template <bool MIXED, int MINB>
 cudaError_t persistent_occupancy(const Stencils& st, int* per_sm) {
   const size_t smem = persistent_smem_bytes(st, MIXED);
@@ -133,7 +135,8 @@ cudaError_t configure_interact_kernels() {
 cudaError_t launch_interior_items(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
   if (a.n_interior == 0) return cudaSuccess;
   if (a.mixed)
-    k_interior_items<true><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp, a.mp32, a.loc);
+    k_interior_items<true><<<2 * a.n_interior, items::kThreads, items::interior_smem_bytes(), s>>>(
+        t, a.interior, a.st, a.mp, a.mp32, a.loc);
   else
     k_interior_items<false><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp, a.mp32, a.loc);
   return cudaGetLastError();

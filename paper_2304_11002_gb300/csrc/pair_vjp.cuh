@@ -21,7 +21,11 @@ __host__ __device__ __forceinline__ void m2l_pair_vjp(const double R0, const dou
                                                       const double m, const double* Q, const double* O,
                                                       const double* Oh, const double* Lb, PairVJP& out) {
   // ---- forward intermediates
+#ifdef __CUDA_ARCH__
+  const double rinv = rsqrt_f64(fma(R0, R0, fma(R1, R1, R2 * R2)));  // as the forward kernels
+#else
   const double rinv = 1.0 / sqrt(R0 * R0 + R1 * R1 + R2 * R2);
+#endif
   const double ir2 = rinv * rinv;
   const double f0 = rinv, f1 = -rinv * ir2, f2 = -3.0 * f1 * ir2, f3 = -5.0 * f2 * ir2, f4 = -7.0 * f3 * ir2;
   const double xx = R0 * R0, xy = R0 * R1, xz = R0 * R2, yy = R1 * R1, yz = R1 * R2, zz = R2 * R2;
