@@ -121,7 +121,7 @@ struct octo_fmm {
   double *d_mp = nullptr, *d_loc = nullptr;
   float* d_mp32 = nullptr;    // float32 multipoles (mixed precision only)
   double* d_near = nullptr;   // [4][leaf cells] near-field sums (mixed precision only)
-  float4* d_kappa32 = nullptr;
+  float4* d_leaf_k32 = nullptr;  // mixed only: inline float32 kernel rows of the leaf far tables
   DevTree dt;
   Stencils st;
   bool forward_done = false;
@@ -174,7 +174,7 @@ void free_all(octo_fmm* h) {
                   h->d_bnd_index, h->d_mpb,    h->d_locb,
                   h->d_general,  h->d_queue,   h->d_counter, h->d_err,
                   h->d_leaf_far, h->d_leaf_root, h->d_leaf_near,
-                  h->d_kappa32};
+                  h->d_leaf_k32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int64_t* p : {h->xg.d_ft, h->xg.d_fs, h->xg.d_fm, h->xg.d_fsrc, h->xg.d_lt, h->xg.d_ls, h->xg.d_lm,
@@ -648,12 +648,6 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     for (int k = 0; k < 3; ++k) R = std::max(R, std::abs((int)(int8_t)((v >> (8 * k)) & 0xff)));
   std::vector<Kappa> kap = make_kappa(R);
   up(&h->d_kappa, kap);
-  {
-    std::vector<float4> k32(kap.size());
-    for (size_t i = 0; i < kap.size(); ++i)
-      k32[i] = make_float4((float)kap[i].v[0], (float)kap[i].v[1], (float)kap[i].v[2], (float)kap[i].v[3]);
-    up(&h->d_kappa32, k32);
-  }
   if (e == cudaSuccess) e = upload_cross(P, P.xg_targets, P.xg_start, P.xg_mid, P.xg_sources, h->xg);
   up(&h->d_xc_t, P.xc_targets);
   up(&h->d_xc_off, P.xc_slice_off);
@@ -705,6 +699,16 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     e = upload(&h->d_leaf_far, lf);
     if (e == cudaSuccess) e = upload(&h->d_leaf_root, lr);
     if (e == cudaSuccess) e = upload(&h->d_leaf_near, ln);
+    if (precision == OCTO_MIXED) {  // float32 kernel rows inline: far entries, then root entries
+      std::vector<float4> k32;
+      k32.reserve(lf.size() + lr.size());
+      for (const std::vector<int2>* tab : {&lf, &lr})
+        for (const int2& en : *tab) {
+          const Kappa& v = kap[en.y];
+          k32.push_back(make_float4((float)v.v[0], (float)v.v[1], (float)v.v[2], (float)v.v[3]));
+        }
+      if (e == cudaSuccess) e = upload(&h->d_leaf_k32, k32);
+    }
     if (e != cudaSuccess) {
       std::string m = std::string("device setup failed: ") + cudaGetErrorString(e);
       free_all(h);
@@ -713,7 +717,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     }
   }
   h->st = Stencils{h->d_st_parity, P.n_st,       h->d_st_root,   (int)P.st_root.size(), h->d_st_near,
-                   (int)P.st_near.size(), h->d_kappa, h->d_kappa32, R, RN, h->d_cell_ent, h->d_cell_ent_off,
+                   (int)P.st_near.size(), h->d_kappa, h->d_leaf_k32, R, RN, h->d_cell_ent, h->d_cell_ent_off,
                    h->d_bnd_perm, h->d_bnd_index, h->d_leaf_far, h->d_leaf_root, h->d_leaf_near};
   h->xc = CrossCells{h->d_xc_t, h->d_xc_off, h->d_xc_ent, h->d_xc_tab, (int)(P.xc_slice_off.size() - 1),
                      (int)(P.xc_table.size() / 4), h->d_xc_counter};

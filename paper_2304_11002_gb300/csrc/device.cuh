@@ -32,12 +32,26 @@ struct DevTree {
 
 // Float32 copy of the multipoles used by the mixed-precision far field, in units of
 // the cell width h of the cell's level (so that float32 neither overflows nor
-// underflows whatever the physical units), cell-major so that one source is five
-// 16-byte loads from one address:
-//   mp32 [NC][20]  m, x = (X - c_node) / h (c_node = geometric centre of the node),
-//                  Q / h^2, O / h^3   (same field order as mp; 80 bytes per cell).
+// underflows whatever the physical units): per cell the 20 values
+//   m, x = (X - c_node) / h (c_node = geometric centre of the node), Q / h^2, O / h^3
+// (same field order as mp), as five float4 planes per node:
+//   mp32 float4 [n_nodes][5][512]   plane k holds values 4k .. 4k + 3,
+// with the 512 cells of a node in parity-major order (mp32_slot): the 64 cells of
+// one parity class (a & 1, b & 1, c & 1) are contiguous, a >> 1 fastest.  The
+// lanes of a parity-class warp hold consecutive (a >> 1, b >> 1, c >> 1), so at any
+// stencil offset they read runs of consecutive 16-byte words of each plane, and
+// the five planes of a source are one address plus constant offsets.
 // Node centres of same-level neighbours differ by exactly 8 h per axis.
-constexpr int kMp32Stride = 20;
+constexpr int kMp32Planes = 5;
+
+__host__ __device__ __forceinline__ int mp32_slot(int a, int b, int c) {
+  return ((a & 1) + 2 * (b & 1) + 4 * (c & 1)) * 64 + (a >> 1) + 4 * (b >> 1) + 16 * (c >> 1);
+}
+
+// Plane 0 of local cell (a, b, c), 0 <= a, b, c < 8, of node `node`, as a float4 index.
+__host__ __device__ __forceinline__ int64_t mp32_base(int node, int a, int b, int c) {
+  return (int64_t)node * (kMp32Planes * 512) + mp32_slot(a, b, c);
+}
 
 // Compensated float32 sum (Kahan): s holds the running sum, c the negative of the
 // rounding error not yet added back; the exact sum is s - c to float32 working

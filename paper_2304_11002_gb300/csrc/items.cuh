@@ -122,11 +122,11 @@ __device__ __forceinline__ void flush_partial(Acc<float>& a, float2* __restrict_
   acc_zero(a);
 }
 
-// One float32 source record (cell-major layout, see device.cuh).
-__device__ __forceinline__ void load_mp32(const float* __restrict__ mp32, int64_t cell, float& m, float x[3],
+// One float32 source record (five planes, see device.cuh); base = mp32_base(...).
+__device__ __forceinline__ void load_mp32(const float* __restrict__ mp32, int64_t base, float& m, float x[3],
                                           float Q[6], float O[10]) {
-  const float4* r = reinterpret_cast<const float4*>(mp32 + cell * kMp32Stride);
-  const float4 v0 = __ldg(r), v1 = __ldg(r + 1), v2 = __ldg(r + 2), v3 = __ldg(r + 3), v4 = __ldg(r + 4);
+  const float4* r = reinterpret_cast<const float4*>(mp32) + base;
+  const float4 v0 = __ldg(r), v1 = __ldg(r + 512), v2 = __ldg(r + 1024), v3 = __ldg(r + 1536), v4 = __ldg(r + 2048);
   m = v0.x, x[0] = v0.y, x[1] = v0.z, x[2] = v0.w;
   Q[0] = v1.x, Q[1] = v1.y, Q[2] = v1.z, Q[3] = v1.w, Q[4] = v2.x, Q[5] = v2.y;
   O[0] = v2.z, O[1] = v2.w, O[2] = v3.x, O[3] = v3.y, O[4] = v3.z, O[5] = v3.w;
@@ -142,7 +142,7 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
   const int64_t NC = t.NC;
   const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
   float mA, xA[3], QA[6], Oh[10], tOh[3];
-  load_mp32(mp32, tgt, mA, xA, QA, Oh);
+  load_mp32(mp32, mp32_base(node, a, b, c), mA, xA, QA, Oh);
   {
     const float inv_m = 1.0f / mA;
     for (int i = 0; i < 10; ++i) Oh[i] *= inv_m;
@@ -166,9 +166,8 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
       const int ox = sa >> 3, oy = sb >> 3, oz = sc >> 3;
       const int snode = __ldg(nb + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
       if (snode < 0) continue;
-      const int64_t src = (int64_t)snode * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
       float m, x[3], Q[6], O[10];
-      load_mp32(mp32, src, m, x, Q, O);
+      load_mp32(mp32, mp32_base(snode, sa & 7, sb & 7, sc & 7), m, x, Q, O);
       const float R0 = xA[0] - (x[0] + 8.0f * (float)ox);
       const float R1 = xA[1] - (x[1] + 8.0f * (float)oy);
       const float R2 = xA[2] - (x[2] + 8.0f * (float)oz);
@@ -282,8 +281,8 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
   const int* nb = t.nbr + 27 * node;
   T xA0, xA1, xA2;
   if constexpr (MIXED) {
-    xA0 = mp32[tgt * kMp32Stride + F_X + 0], xA1 = mp32[tgt * kMp32Stride + F_X + 1],
-    xA2 = mp32[tgt * kMp32Stride + F_X + 2];
+    const float4 v = __ldg(reinterpret_cast<const float4*>(mp32) + mp32_base(node, a, b, c));
+    xA0 = v.y, xA1 = v.z, xA2 = v.w;
   } else {
     xA0 = mp[(F_X + 0) * NC + tgt], xA1 = mp[(F_X + 1) * NC + tgt], xA2 = mp[(F_X + 2) * NC + tgt];
   }
@@ -304,7 +303,7 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
       T R0, R1, R2, m, Q[6], O[10], rinv;
       if constexpr (MIXED) {
         float x[3];
-        load_mp32(mp32, src, m, x, Q, O);
+        load_mp32(mp32, mp32_base(sn, sa & 7, sb & 7, sc & 7), m, x, Q, O);
         R0 = xA0 - (x[0] + 8.0f * (float)ox);
         R1 = xA1 - (x[1] + 8.0f * (float)oy);
         R2 = xA2 - (x[2] + 8.0f * (float)oz);
@@ -424,6 +423,7 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
     // two halo reads and eight fused multiply-adds)
     const int lane = threadIdx.x & 31;
     const int2* __restrict__ far = (lvl == 0 ? st.leaf_root : st.leaf_far) + (threadIdx.x >> 5) * n_far;
+    const float4* __restrict__ fk = st.leaf_k32 + (lvl == 0 ? 8 * st.n_st : 0) + (threadIdx.x >> 5) * n_far;
     const int lane_f = (lane & 3) + gf.PY * ((lane >> 2) & 3) + gf.PZ * (lane >> 4);
     const int dz = 2 * gf.PZ;
     KF f[2][4];
@@ -436,9 +436,9 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
       float pa[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
       for (int s = s0i; s < s1i; ++s) {
-        const int2 e = __ldg(far + s);
-        const float m0 = halo32[lane_f + e.x], m1 = halo32[lane_f + e.x + dz];
-        const float4 k = __ldg(st.kappa32 + e.y);
+        const int off = __ldg(&far[s].x);
+        const float4 k = __ldg(fk + s);
+        const float m0 = halo32[lane_f + off], m1 = halo32[lane_f + off + dz];
         pa[0] = fmaf(m0, k.x, pa[0]);
         pa[1] = fmaf(m0, k.y, pa[1]);
         pa[2] = fmaf(m0, k.z, pa[2]);

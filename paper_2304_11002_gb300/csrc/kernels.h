@@ -22,7 +22,9 @@ struct Stencils {
   const int* near_;   // non-zero near offsets
   int n_near;
   const Kappa* kappa;    // dense monopole kernel table over [-R, R]^3, unit cell width
-  const float4* kappa32; // the same table rounded to float32
+  const float4* leaf_k32; // mixed path: the float32 kernel row of every leaf_far entry
+                          // ([8][n_st]), then of every leaf_root entry ([8][n_root]),
+                          // inline in table order (no dependent row lookup)
   int radius;            // R: maximum |offset component|
   int near_radius;       // maximum |offset component| of the near offsets
   const int* cell_ent;   // parity offsets per (cell, neighbour slot), see Plan::cell_ent
@@ -30,7 +32,7 @@ struct Stencils {
   const unsigned short* bnd_perm;  // per boundary leaf node: cells of each half by decreasing load
   const int* bnd_index;            // per node: row of bnd_perm or -1
   // Leaf items, per parity class p of the target cell and stencil entry s:
-  // {offset into the shared-memory mass halo, row of kappa / kappa32} (see items.cuh).
+  // {offset into the shared-memory mass halo, row of kappa} (see items.cuh).
   const int2* leaf_far;   // [8][n_st]   parity stencil (far halo)
   const int2* leaf_root;  // [8][n_root] level-0 stencil (far halo)
   const int2* leaf_near;  // [8][n_near] near offsets (mixed: near float64 halo; float64: far halo)
