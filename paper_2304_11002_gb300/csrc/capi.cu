@@ -228,6 +228,9 @@ int64_t m2l_pair_flops() {
   return g_counted_ops + 3 + 5 + 8;
 }
 constexpr int64_t kConvFlopsPerPair = 8;  // four fused multiply-adds
+// near offsets run as (d, -d) pairs: one add, one subtract and four fused
+// multiply-adds per two pairs
+constexpr int64_t kNearFlopsPer2Pairs = 2 + 4 * 2;
 // Tree passes, float64 in both modes, counted from the expressions of k_m2m / k_l2l
 // as written (FMA = 2): M2M per parent cell = 8 children x (mass and centre sums 7,
 // d 3, m d 3, M2 18, M3 64) + 3 divisions; L2L per cell = d 3, (L3 d) 30, (L3 d d)
@@ -256,12 +259,12 @@ void make_stages(octo_fmm* h) {
       case S_M2L: far = pairs * f_int; break;
       case S_CONV:  // mixed precision: the near field is the separate S_NEAR stage
         far = P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
-        if (h->precision != OCTO_MIXED) near = P.kernel_pairs[2] * kConvFlopsPerPair;
+        if (h->precision != OCTO_MIXED) near = P.kernel_pairs[2] * kNearFlopsPer2Pairs / 2;
         break;
-      case S_NEAR: near = P.kernel_pairs[2] * kConvFlopsPerPair; break;
+      case S_NEAR: near = P.kernel_pairs[2] * kNearFlopsPer2Pairs / 2; break;
       case S_PERSIST:
         far = P.kernel_pairs[0] * f_int + P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
-        near = P.kernel_pairs[2] * kConvFlopsPerPair;
+        near = P.kernel_pairs[2] * kNearFlopsPer2Pairs / 2;
         break;
       case S_CROSS_CELLS: near = pairs * kConvFlopsPerPair; break;  // float64 in both modes
       case S_CROSS_FULL:

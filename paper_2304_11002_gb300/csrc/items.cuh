@@ -290,12 +290,22 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
   // mixed path: partial sums of L0, L1, dg (the only fields a leaf target gets)
   LeafAcc<float> part = {0.0f, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
   int n_part = 0;
-  for (int o = 0; o < 27; ++o) {
-    const int sn = nb[o];
-    if (sn < 0 || t.children[8 * sn] < 0) continue;  // refined neighbours only
-    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-    const int e0 = __ldg(st.cell_ent_off + l * 27 + o), e1 = __ldg(st.cell_ent_off + l * 27 + o + 1);
-    for (int e = e0; e < e1; ++e) {
+  // One flat walk over the (refined neighbour slot, entry) pairs of this cell: the
+  // lanes of a warp (cells of similar total load) advance to their next slot
+  // independently, so a warp runs as many iterations as its busiest lane rather
+  // than the sum over slots of the per-slot maxima.  Each cell still takes its
+  // pairs in slot order, then entry order.
+  int o = -1, e = 0, e1 = 0, sn = -1, ox = 0, oy = 0, oz = 0;
+  for (;;) {
+    while (e == e1 && o < 27) {  // next refined neighbour slot of this cell
+      if (++o == 27) break;
+      sn = nb[o];
+      if (sn < 0 || t.children[8 * sn] < 0) continue;  // refined neighbours only
+      ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+      e = __ldg(st.cell_ent_off + l * 27 + o), e1 = __ldg(st.cell_ent_off + l * 27 + o + 1);
+    }
+    if (o == 27) break;
+    {
       int dx, dy, dz;
       unpack(__ldg(st.cell_ent + e), dx, dy, dz);
       const int sa = a + dx, sb = b + dy, sc = c + dz;
@@ -327,6 +337,7 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
         m2l_pair<false, false>(R0, R1, R2, m, Q, O, zero10, zero10, rinv, acc);
       }
     }
+    ++e;
   }
   if constexpr (MIXED) leaf_merge(acc, part);
 }
@@ -465,19 +476,26 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
       const int2* __restrict__ nr = st.leaf_near + p * st.n_near;
       const int lane_f = (a >> 1) + gf.PY * (b >> 1) + gf.PZ * (c >> 1);
       double s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // unit cell width
-      for (int pass = 0; pass < 2; ++pass) {
-        const int2* __restrict__ tb = pass == 0 ? far : nr;
-        const int nt = pass == 0 ? n_far : st.n_near;
-        for (int s = 0; s < nt; ++s) {
-          const int2 e = __ldg(tb + s);
-          const double m = halo64[lane_f + e.x];
-          const double2* kp = reinterpret_cast<const double2*>(st.kappa + e.y);
-          const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
-          s0 = fma(m, ka.x, s0);
-          s1 = fma(m, ka.y, s1);
-          s2 = fma(m, kb.x, s2);
-          s3 = fma(m, kb.y, s3);
-        }
+      for (int s = 0; s < n_far; ++s) {
+        const int2 e = __ldg(far + s);
+        const double m = halo64[lane_f + e.x];
+        const double2* kp = reinterpret_cast<const double2*>(st.kappa + e.y);
+        const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
+        s0 = fma(m, ka.x, s0);
+        s1 = fma(m, ka.y, s1);
+        s2 = fma(m, kb.x, s2);
+        s3 = fma(m, kb.y, s3);
+      }
+      for (int s = 0; s < st.n_near; s += 2) {  // (d, -d) pairs, as in near_item
+        const int2 e = __ldg(nr + s), f = __ldg(nr + s + 1);
+        const double mp_ = halo64[lane_f + e.x], mm = halo64[lane_f + f.x];
+        const double2* kp = reinterpret_cast<const double2*>(st.kappa + e.y);
+        const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
+        const double sum = mp_ + mm, dif = mp_ - mm;
+        s0 = fma(sum, ka.x, s0);
+        s1 = fma(dif, ka.y, s1);
+        s2 = fma(dif, kb.x, s2);
+        s3 = fma(dif, kb.y, s3);
       }
       L0[half] = s0 * ih;
       L1[half][0] = s1 * ih2;
@@ -487,14 +505,23 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
   }
   double dg[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
   if (any_refined) {  // block-uniform
-    // Boundary pairs with the threads re-assigned to the cells of each half in
-    // decreasing order of load (balanced warps); the results go back to the owning
-    // threads through shared memory (the halo is no longer needed).
+    // Boundary pairs: the node's cells in decreasing order of load, in groups of 32
+    // (one cell per lane, similar loads within a warp), claimed by the warps one
+    // group at a time from a shared counter, heaviest first, so that the block
+    // waits for about max(heaviest group, total / warps) rather than for one warp
+    // holding several heavy groups.  The results go back to the owning threads
+    // through shared memory (the halo is no longer needed).
+    __shared__ int next_group;
+    if (threadIdx.x == 0) next_group = 0;
     __syncthreads();
     double* res = reinterpret_cast<double*>(smem);  // [512][7]
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int lb = st.bnd_perm[(int64_t)st.bnd_index[node] * 512 + half * 256 + threadIdx.x];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+      int g = 0;
+      if (lane == 0) g = atomicAdd(&next_group, 1);
+      g = __shfl_sync(0xffffffffu, g, 0);
+      if (g >= 512 / 32) break;
+      const int lb = st.bnd_perm[(int64_t)st.bnd_index[node] * 512 + g * 32 + lane];
       double v[7];
       if constexpr (MIXED) {
         Acc<KF> acc;
@@ -552,16 +579,20 @@ __device__ __forceinline__ void near_item(const DevTree& t, int node, const Sten
     const int2* __restrict__ nr = st.leaf_near + p * st.n_near;
     const int lane = (a >> 1) + gn.PY * (b >> 1) + gn.PZ * (c >> 1);
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    // entries come in (d, -d) pairs; kappa(-d) = (kappa0(d), -kappa1(d)), so a pair
+    // takes one sum and one difference of its masses and four fused multiply-adds
+    // (six float64 operations for two pairs instead of eight)
 #pragma unroll 2
-    for (int s = 0; s < st.n_near; ++s) {
-      const int2 e = __ldg(nr + s);
-      const double m = halo[lane + e.x];
+    for (int s = 0; s < st.n_near; s += 2) {
+      const int2 e = __ldg(nr + s), f = __ldg(nr + s + 1);
+      const double mp_ = halo[lane + e.x], mm = halo[lane + f.x];
       const double2* kp = reinterpret_cast<const double2*>(st.kappa + e.y);
       const double2 ka = __ldg(kp), kb = __ldg(kp + 1);
-      s0 = fma(m, ka.x, s0);
-      s1 = fma(m, ka.y, s1);
-      s2 = fma(m, kb.x, s2);
-      s3 = fma(m, kb.y, s3);
+      const double sum = mp_ + mm, dif = mp_ - mm;
+      s0 = fma(sum, ka.x, s0);
+      s1 = fma(dif, ka.y, s1);
+      s2 = fma(dif, kb.x, s2);
+      s3 = fma(dif, kb.y, s3);
     }
     const int64_t k = lid * 512 + a + 8 * b + 64 * c;
     nearf[k] = s0 * ih;

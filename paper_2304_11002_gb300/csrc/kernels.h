@@ -29,7 +29,7 @@ struct Stencils {
   int near_radius;       // maximum |offset component| of the near offsets
   const int* cell_ent;   // parity offsets per (cell, neighbour slot), see Plan::cell_ent
   const int* cell_ent_off;
-  const unsigned short* bnd_perm;  // per boundary leaf node: cells of each half by decreasing load
+  const unsigned short* bnd_perm;  // per boundary leaf node: its 512 cells by decreasing load
   const int* bnd_index;            // per node: row of bnd_perm or -1
   // Leaf items, per parity class p of the target cell and stencil entry s:
   // {offset into the shared-memory mass halo, row of kappa} (see items.cuh).

@@ -47,13 +47,16 @@ __global__ void k_p2m(DevTree t, const int* __restrict__ nodes, const double* __
 // Parent cell from its 2x2x2 child cells (parallel-axis rule about the centre of
 // mass): m = sum m_c, X = sum m_c X_c / m, d_c = X_c - X,
 // M2 = sum (M2_c + m_c d d), M3 = sum (M3_c + 3 sym(M2_c d) + m_c d d d).
-// (registers capped for 3 resident blocks per SM so that enough warps keep loads
-// in flight; the children loop of the moments stays rolled)
-__global__ void __launch_bounds__(256, 3) k_m2m(DevTree t, int node_begin, double* __restrict__ mp,
-                                                float* __restrict__ mp32) {
-  const int node = node_begin + (blockIdx.x >> 1);
+// One thread per parent cell, blocks of 64 threads (eight per node): the pass is
+// float64-bound, and a coarse level of one or a few nodes then still spreads over
+// eight SMs per node instead of two.  Registers capped at the same 80 as three
+// 256-thread blocks per SM; the children loop of the moments stays rolled.
+constexpr int kM2MThreads = 64;
+__global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_begin, double* __restrict__ mp,
+                                                        float* __restrict__ mp32) {
+  const int node = node_begin + (blockIdx.x >> 3);
   if (t.children[8 * node] < 0) return;
-  const int l = ((blockIdx.x & 1) << 8) + threadIdx.x;
+  const int l = ((blockIdx.x & 7) * kM2MThreads) + threadIdx.x;
   const int a = l & 7, b = (l >> 3) & 7, c = l >> 6;
   const int o = (a >> 2) + 2 * (b >> 2) + 4 * (c >> 2);
   const int ch = t.children[8 * node + o];
@@ -228,7 +231,7 @@ cudaError_t launch_p2m(const DevTree& t, const int* leaf_nodes, int n, const dou
 
 cudaError_t launch_m2m(const DevTree& t, int b, int e, double* mp, float* mp32, cudaStream_t s) {
   if (e <= b) return cudaSuccess;
-  k_m2m<<<2 * (e - b), 256, 0, s>>>(t, b, mp, mp32);
+  k_m2m<<<(512 / kM2MThreads) * (e - b), kM2MThreads, 0, s>>>(t, b, mp, mp32);
   return cudaGetLastError();
 }
 

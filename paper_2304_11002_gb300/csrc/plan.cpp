@@ -345,6 +345,26 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
         else if (dx || dy || dz)
           P.st_near.push_back(pack_offset(dx, dy, dz));
       }
+  {  // near offsets as (d, -d) pairs: the near item sums a pair's two masses for the
+     // potential and differences them for the field (kernel rows of -d are those of
+     // d with the gradient part negated).  The set is symmetric and was generated in
+     // lexicographic order, so entry k and entry n - 1 - k are negatives.
+    const std::vector<int32_t> lex = P.st_near;
+    const size_t nn = lex.size();
+    P.st_near.clear();
+    for (size_t k = 0; k < nn / 2; ++k) {
+      P.st_near.push_back(lex[k]);
+      P.st_near.push_back(lex[nn - 1 - k]);
+    }
+    bool paired = nn % 2 == 0;
+    for (size_t k = 0; paired && k < nn; k += 2)
+      for (int b = 0; b < 3; ++b)
+        paired = paired && (int8_t)((P.st_near[k] >> (8 * b)) & 0xff) == -(int8_t)((P.st_near[k + 1] >> (8 * b)) & 0xff);
+    if (!paired) {
+      P.error = "near offsets are not symmetric";
+      return OCTO_EINVAL;
+    }
+  }
   // per-cell entry lists by neighbour slot
   P.cell_ent.clear();
   P.cell_ent_off.assign(1, 0);
@@ -393,13 +413,10 @@ int build_plan(const octo_tree_desc* desc, double theta, Plan& P) {
         const int m = P.nbr[27 * k + o];
         if (m >= 0 && P.children[8 * m] >= 0) load[l] += cell_cnt[l * 27 + o];
       }
-    for (int half = 0; half < 2; ++half) {
-      std::vector<int> cells;
-      for (int l = 0; l < kCells; ++l)
-        if ((l >> 6 & 1) == half) cells.push_back(l);
-      std::stable_sort(cells.begin(), cells.end(), [&](int x, int y) { return load[x] > load[y]; });
-      for (int i = 0; i < 256; ++i) P.bnd_perm[bi * kCells + half * 256 + i] = (uint16_t)cells[i];
-    }
+    std::vector<int> cells(kCells);
+    for (int l = 0; l < kCells; ++l) cells[l] = l;
+    std::stable_sort(cells.begin(), cells.end(), [&](int x, int y) { return load[x] > load[y]; });
+    for (int i = 0; i < kCells; ++i) P.bnd_perm[bi * kCells + i] = (uint16_t)cells[i];
   }
 
   // ---------------- same-level counts ----------------

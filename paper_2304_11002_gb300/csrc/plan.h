@@ -50,7 +50,7 @@ struct Plan {
   // Leaf nodes with refined same-level neighbours: per node, the 256 cells of each
   // half (even / odd z) ordered by decreasing number of pairs with those
   // neighbours, so that the lanes of a warp get similar trip counts.
-  std::vector<uint16_t> bnd_perm;   // [n_boundary][2][256] local cell indices
+  std::vector<uint16_t> bnd_perm;   // [n_boundary][512] local cells by decreasing boundary load
   std::vector<int32_t> bnd_index;   // per device node: row of bnd_perm, or -1
 
   // ---- work lists ----
