@@ -121,6 +121,7 @@ struct octo_fmm {
   double *d_mp = nullptr, *d_loc = nullptr;
   float* d_mp32 = nullptr;    // float32 multipoles (mixed precision only)
   double* d_near = nullptr;   // [4][leaf cells] near-field sums (mixed precision only)
+  double* d_xcf = nullptr;    // [4][32 x cross slices] sums of the persistent kernel's cross items
   float4* d_leaf_k32 = nullptr;  // mixed only: inline float32 kernel rows of the leaf far tables
   DevTree dt;
   Stencils st;
@@ -169,7 +170,7 @@ void free_all(octo_fmm* h) {
   void* ptrs[] = {h->d_level,    h->d_parent,  h->d_octant, h->d_children, h->d_nbr,    h->d_leaf_id,
                   h->d_ijk,      h->d_interior, h->d_leaf,  h->d_boundary, h->d_st_parity, h->d_st_root,
                   h->d_st_near,  h->d_kappa,   h->d_xc_t,   h->d_xc_off,   h->d_xc_ent,  h->d_xc_tab,  h->d_xc_counter,
-                  h->d_mp,       h->d_loc,      h->d_io,        h->d_mp32,     h->d_near,
+                  h->d_mp,       h->d_loc,      h->d_io,        h->d_mp32,     h->d_near,     h->d_xcf,
                   h->d_cell_ent, h->d_cell_ent_off, h->d_bnd_perm,
                   h->d_bnd_index, h->d_mpb,    h->d_locb,
                   h->d_general,  h->d_queue,   h->d_counter, h->d_err,
@@ -262,9 +263,9 @@ void make_stages(octo_fmm* h) {
         if (h->precision != OCTO_MIXED) near = P.kernel_pairs[2] * kNearFlopsPer2Pairs / 2;
         break;
       case S_NEAR: near = P.kernel_pairs[2] * kNearFlopsPer2Pairs / 2; break;
-      case S_PERSIST:
+      case S_PERSIST:  // including the tabulated cross-level pairs (cross items)
         far = P.kernel_pairs[0] * f_int + P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
-        near = P.kernel_pairs[2] * kNearFlopsPer2Pairs / 2;
+        near = P.kernel_pairs[2] * kNearFlopsPer2Pairs / 2 + (h->xc.n_slices > 0 ? P.xc_pairs * kConvFlopsPerPair : 0);
         break;
       case S_CROSS_CELLS: near = pairs * kConvFlopsPerPair; break;  // float64 in both modes
       case S_CROSS_FULL:
@@ -298,7 +299,9 @@ void make_stages(octo_fmm* h) {
   const bool mixed = h->precision == OCTO_MIXED;
   if (h->mode == MODE_PERSISTENT) {
     add(S_PERSIST, 0, 0, mixed ? "interact_persistent_mixed" : "interact_persistent",
-        P.kernel_pairs[0] + P.kernel_pairs[1] + P.kernel_pairs[2] + P.kernel_pairs[3], (int64_t)P.n_nodes * kCells);
+        P.kernel_pairs[0] + P.kernel_pairs[1] + P.kernel_pairs[2] + P.kernel_pairs[3] +
+            (h->xc.n_slices > 0 ? P.xc_pairs : 0),
+        (int64_t)P.n_nodes * kCells);
   } else {
     if (!P.interior_nodes.empty())
       add(S_M2L, 0, 0, mixed ? "m2l_interior_f32" : "m2l_interior", P.kernel_pairs[0],
@@ -316,7 +319,10 @@ void make_stages(octo_fmm* h) {
   if (h->xc.n_slices > 0) {
     int64_t nt = 0;
     for (int64_t t : P.xc_targets) nt += t >= 0;
-    add(S_CROSS_CELLS, 0, 0, "cross_cells", P.xc_pairs, nt);
+    if (h->mode == MODE_PERSISTENT)
+      add(S_CROSS_CELLS, 0, 0, "cross_cells_apply", 0, nt);
+    else
+      add(S_CROSS_CELLS, 0, 0, "cross_cells", P.xc_pairs, nt);
   }
   if (h->xg.n_f > 0) add(S_CROSS_FULL, 0, 0, "cross_interior", h->xg.f_pairs, h->xg.n_f);
   if (h->xg.n_l > 0) add(S_CROSS_LEAF, 0, 0, "cross_leaf", h->xg.l_pairs, h->xg.n_l);
@@ -362,6 +368,8 @@ InteractArgs interact_args(const octo_fmm* h) {
   a.counter = h->d_counter;
   a.grid = h->n_sm * h->persist_per_sm[h->min_blocks];
   a.min_blocks = h->min_blocks;
+  a.xc = h->xc;
+  a.xcf = h->d_xcf;
   return a;
 }
 
@@ -375,7 +383,9 @@ cudaError_t enq_stage(octo_fmm* h, const octo_fmm::Stage& st, const double* rho,
     case S_CONV: return launch_leaf_items(h->dt, interact_args(h), s);
     case S_NEAR: return launch_near_items(h->dt, interact_args(h), s);
     case S_PERSIST: return launch_persistent(h->dt, interact_args(h), s);
-    case S_CROSS_CELLS: return launch_cross_cells(h->dt, h->xc, h->d_mp, h->d_loc, h->xc_grid, s);
+    case S_CROSS_CELLS:  // persistent mode: the sums came from the queue's cross items
+      if (h->mode == MODE_PERSISTENT) return launch_cross_apply(h->dt, h->xc, h->d_xcf, h->d_loc, s);
+      return launch_cross_cells(h->dt, h->xc, h->d_mp, h->d_loc, h->xc_grid, s);
     case S_CROSS_FULL:
       return launch_cross_list(h->dt, h->xg.f, true, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
     case S_CROSS_LEAF:
@@ -447,25 +457,28 @@ namespace {
 // Work of the persistent queue's items, in any common unit: per M2L pair of an
 // interior item, per leaf node for the far-field item and for the near item.
 struct ItemCosts {
-  double interior_pair, leaf_far, leaf_near;
+  double interior_pair, leaf_far, leaf_near, cross_pair;
 };
 
 // Estimates before measurement, in SM cycles: an M2L pair with correction ~240
 // float32 instructions at 128 per cycle; a leaf node's far field ~1200 entries x 512
 // cells at ~24 instructions per pair (halo staging and boundary pairs included); its
-// near field 170 x 512 pairs of 4 DFMA at 2 per cycle, at about 60 % of that rate
-// when it shares the SM.
+// near field 170 x 512 pairs of 3 float64 operations at 2 per cycle, at about 60 %
+// of that rate when it shares the SM; a tabulated cross-level pair 4 DFMA, likewise.
 ItemCosts default_costs(const Plan& P) {
-  return {240.0 / 128.0, 512.0 * P.n_st * 24.0 / 128.0, 512.0 * (double)P.st_near.size() * 4.0 / 2.0 * 0.6};
+  return {240.0 / 128.0, 512.0 * P.n_st * 24.0 / 128.0, 512.0 * (double)P.st_near.size() * 3.0 / 2.0 / 0.6,
+          4.0 / 2.0 / 0.6};
 }
 
 // The persistent work queue (item = (node << 3) | (kind << 1) | half).  Interior
 // items (kind 0, one per half) of the root first (the largest), then of the other
 // levels; leaf items (kind 1, whole node) with refined neighbours before the
-// others.  Float64: all interior items, then all leaf items.  Mixed precision: the
-// float32-bound items (interior, leaf far field) and the float64-bound near items
-// (kind 2) are merged so that every prefix of the queue holds the same fraction of
-// the work of both, so that the two pipes of every SM stay busy side by side.
+// others; cross items (kind 3, kCrossSlicesPerItem slices of the tabulated
+// cross-level pairs, widest first).  Float64: all interior items, then all leaf
+// items, then the cross items.  Mixed precision: the float32-bound items (interior,
+// leaf far field) and the float64-bound items (cross, then near items, kind 2) are
+// merged so that every prefix of the queue holds the same fraction of the work of
+// both, so that the two pipes of every SM stay busy side by side.
 std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c) {
   std::vector<int32_t> q32, q64, q;
   std::vector<double> w32, w64;
@@ -477,6 +490,13 @@ std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c) 
           q32.push_back(item(k, 0, half));
           w32.push_back(256.0 * (P.level[k] == 0 ? (double)P.st_root.size() : (double)P.n_st) * c.interior_pair);
         }
+  const int n_slices = P.xc_slice_off.empty() ? 0 : (int)P.xc_slice_off.size() - 1;
+  if (mixed)  // float64-bound: the cross items head the float64 list
+    for (int ci = 0; ci * kCrossSlicesPerItem < n_slices; ++ci) {
+      const int s1 = std::min((ci + 1) * kCrossSlicesPerItem, n_slices);
+      q64.push_back(item(ci, 3, 0));
+      w64.push_back((double)(P.xc_slice_off[s1] - P.xc_slice_off[ci * kCrossSlicesPerItem]) * c.cross_pair);
+    }
   std::vector<char> bnd(P.n_nodes, 0);
   for (int k : P.boundary_nodes) bnd[k] = 1;
   for (int pass = 0; pass < 2; ++pass)
@@ -489,7 +509,10 @@ std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c) 
           w64.push_back(c.leaf_near);
         }
       }
-  if (!mixed) return q32;
+  if (!mixed) {  // float64: the cross items last
+    for (int ci = 0; ci * kCrossSlicesPerItem < n_slices; ++ci) q32.push_back(item(ci, 3, 0));
+    return q32;
+  }
   double t32 = 0, t64 = 0, c32 = 0, c64 = 0;
   for (double v : w32) t32 += v;
   for (double v : w64) t64 += v;
@@ -554,12 +577,18 @@ int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
     const Plan& P = h->plan;
     h->mode = MODE_PER_KIND;
     e = rebuild_stages(h);
-    float t_int = 0, t_far = 0, t_near = 0;
+    float t_int = 0, t_far = 0, t_near = 0, t_cross = 0;
     if (e == cudaSuccess) e = time_stage(h, S_M2L, ts, t0, t1, &t_int);
     if (e == cudaSuccess) e = time_stage(h, S_CONV, ts, t0, t1, &t_far);
     if (e == cudaSuccess) e = time_stage(h, S_NEAR, ts, t0, t1, &t_near);
+    if (e == cudaSuccess && h->xc.n_slices > 0) e = time_stage(h, S_CROSS_CELLS, ts, t0, t1, &t_cross);
     if (e == cudaSuccess && t_int > 0 && t_far > 0 && t_near > 0 && P.kernel_pairs[0] > 0 && P.n_leaf > 0) {
-      const ItemCosts c = {t_int / (double)P.kernel_pairs[0], t_far / (double)P.n_leaf, t_near / (double)P.n_leaf};
+      // (the cross pairs' cost in the same unit; the default ratio when there are none)
+      const double cross_pair = t_cross > 0 && P.xc_pairs > 0
+                                    ? t_cross / (double)P.xc_pairs
+                                    : t_near / (double)P.n_leaf / default_costs(P).leaf_near * default_costs(P).cross_pair;
+      const ItemCosts c = {t_int / (double)P.kernel_pairs[0], t_far / (double)P.n_leaf, t_near / (double)P.n_leaf,
+                           cross_pair};
       const std::vector<int32_t> q = build_queue(P, true, c);
       if ((int)q.size() == h->n_items)
         e = cudaMemcpyAsync(h->d_queue, q.data(), sizeof(int32_t) * q.size(), cudaMemcpyHostToDevice, ts);
@@ -666,6 +695,8 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   if (e == cudaSuccess) e = cudaMalloc(&h->d_loc, sizeof(double) * N_LOC * NC);
   if (e == cudaSuccess && precision == OCTO_MIXED) e = cudaMalloc(&h->d_mp32, sizeof(float) * N_MP * NC);
   if (e == cudaSuccess && precision == OCTO_MIXED) e = cudaMalloc(&h->d_near, sizeof(double) * 4 * h->n_leaf_cells());
+  if (e == cudaSuccess && P.xc_slice_off.size() > 1)
+    e = cudaMalloc(&h->d_xcf, sizeof(double) * 4 * 32 * (P.xc_slice_off.size() - 1));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_io, sizeof(double) * 5 * h->n_leaf_cells());
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -744,7 +775,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = configure_interact_kernels();
     for (int mb = 1; mb <= (precision == OCTO_MIXED ? 3 : 2) && e == cudaSuccess; ++mb)
-      e = persistent_blocks_per_sm(precision == OCTO_MIXED, mb, h->st, &h->persist_per_sm[mb]);
+      e = persistent_blocks_per_sm(precision == OCTO_MIXED, mb, h->st, h->xc, &h->persist_per_sm[mb]);
     int xc_per_sm = 0;
     if (e == cudaSuccess && h->xc.n_slices > 0) e = cross_cells_blocks_per_sm(h->xc, &xc_per_sm);
     h->xc_grid = h->n_sm * std::max(xc_per_sm, 1);

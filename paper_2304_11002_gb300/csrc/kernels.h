@@ -61,6 +61,8 @@ struct CrossCells {
   int n_rows;
   int* counter;              // device scratch: next slice to claim (reset by the launcher)
 };
+// Slices of one cross item of the persistent interaction kernel (kind 3).
+constexpr int kCrossSlicesPerItem = 64;
 
 // ------------------------------------------------------------ tree passes (kernels_fp64.cu)
 // mp32 (may be null): float32 copy of the multipoles for the mixed-precision path.
@@ -90,13 +92,16 @@ struct InteractArgs {
   int n_items;
   int* counter;        // work counter of the persistent launch (device scratch)
   int grid;            // blocks of the persistent launch (SMs x resident blocks per SM)
-  int min_blocks;      // launch-bounds variant of the persistent kernel (1 or 2)
+  int min_blocks;      // launch-bounds variant of the persistent kernel (1, 2 or 3)
+  CrossCells xc;       // tabulated cross-level pairs: cross items of the persistent queue
+  double* xcf;         // [4][32 * xc.n_slices] their per-slot sums (persistent mode)
 };
 // Once per process and device (opts the leaf-item kernels into large shared memory).
 cudaError_t configure_interact_kernels();
 // Resident blocks per SM of the persistent kernel variant (also sets its shared
 // memory limit); call outside stream capture.
-cudaError_t persistent_blocks_per_sm(bool mixed, int min_blocks, const Stencils& st, int* per_sm);
+cudaError_t persistent_blocks_per_sm(bool mixed, int min_blocks, const Stencils& st, const CrossCells& xc,
+                                     int* per_sm);
 cudaError_t launch_interior_items(const DevTree& t, const InteractArgs& a, cudaStream_t s);
 cudaError_t launch_leaf_items(const DevTree& t, const InteractArgs& a, cudaStream_t s);
 cudaError_t launch_near_items(const DevTree& t, const InteractArgs& a, cudaStream_t s);  // mixed precision only
@@ -112,6 +117,9 @@ cudaError_t cross_cells_blocks_per_sm(const CrossCells& xc, int* blocks);
 // local-expansion adjoints locb of its partners.
 cudaError_t launch_cross_cells_adjoint(const DevTree& t, const CrossCells& xc, const double* locb, double* mpb,
                                        int grid, cudaStream_t s);
+// The per-slot sums the persistent kernel's cross items left in xcf, added to the targets.
+cudaError_t launch_cross_apply(const DevTree& t, const CrossCells& xc, const double* xcf, double* loc,
+                               cudaStream_t s);
 cudaError_t launch_cross_cells(const DevTree& t, const CrossCells& xc, const double* mp, double* loc, int grid,
                                cudaStream_t s);
 

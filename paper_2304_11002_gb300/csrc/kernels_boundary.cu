@@ -16,7 +16,7 @@
 // the end (deterministic).  M2L partners come first in each list, then P2P partners
 // (exact point-mass interaction, always float64).  Mixed precision runs the M2L part
 // in float32 with compensated sums, operands scaled to the target's cell width.
-#include "kernels.h"
+#include "cross.cuh"
 
 namespace octo {
 
@@ -29,19 +29,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 constexpr int kCrossCellsThreads = 256;
-
-__device__ __forceinline__ double flip_sign(double x, int64_t bit) {
-  return __longlong_as_double(__double_as_longlong(x) ^ (bit << 63));
-}
+using cross::flip_sign;
 
 __global__ void __launch_bounds__(kCrossCellsThreads) k_cross_cells(DevTree t, CrossCells xc,
                                                                     const double* __restrict__ mp,
                                                                     double* __restrict__ loc) {
   extern __shared__ double2 tab2[];  // n_rows x 4 doubles
-  const double2* __restrict__ gt = reinterpret_cast<const double2*>(xc.table);
-  for (int i = threadIdx.x; i < 2 * xc.n_rows; i += blockDim.x) tab2[i] = gt[i];
+  cross::stage_table(xc, tab2);
   __syncthreads();
-  const int64_t NC = t.NC;
   const int lane = threadIdx.x & 31;
   for (;;) {
     // the next slice, claimed by the warp (slices are sorted widest first)
@@ -49,43 +44,20 @@ __global__ void __launch_bounds__(kCrossCellsThreads) k_cross_cells(DevTree t, C
     if (lane == 0) s = atomicAdd(xc.counter, 1);
     s = __shfl_sync(0xffffffffu, s, 0);
     if (s >= xc.n_slices) return;
-    const int64_t o0 = xc.slice_off[s];
-    const int64_t width = (xc.slice_off[s + 1] - o0) >> 5;  // a multiple of 4
-    const int64_t* __restrict__ ent = xc.entries + o0 + lane;
-    double S0 = 0.0, S1 = 0.0, S2 = 0.0, S3 = 0.0;
-    int64_t en[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) en[u] = __ldcs(ent + 32 * u);
-    for (int64_t k = 0; k < width; k += 4) {
-      int64_t e[4];
-      double m[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) e[u] = en[u];
-      if (k + 4 < width) {  // next group's entries, in flight during this group
-#pragma unroll
-        for (int u = 0; u < 4; ++u) en[u] = __ldcs(ent + 32 * (k + 4 + u));
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) m[u] = __ldg(mp + (e[u] >> 20));
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int row = (int)(e[u] & 0xffff);
-        const double2 a = tab2[2 * row], b = tab2[2 * row + 1];
-        S0 = fma(m[u], a.x, S0);
-        S1 = fma(flip_sign(m[u], (e[u] >> 16) & 1), a.y, S1);
-        S2 = fma(flip_sign(m[u], (e[u] >> 17) & 1), b.x, S2);
-        S3 = fma(flip_sign(m[u], (e[u] >> 18) & 1), b.y, S3);
-      }
-    }
-    const int64_t tg = xc.targets[(int64_t)s * 32 + lane];
-    if (tg >= 0) {
-      const double ih = 1.0 / t.h[t.level[tg >> 9]], ih2 = ih * ih;
-      loc[G_L0 * NC + tg] -= S0 * ih;
-      loc[(G_L1 + 0) * NC + tg] += S1 * ih2;
-      loc[(G_L1 + 1) * NC + tg] += S2 * ih2;
-      loc[(G_L1 + 2) * NC + tg] += S3 * ih2;
-    }
+    double S[4];
+    cross::slice_sums(xc, tab2, mp, s, lane, S);
+    cross::apply(t, xc, (int64_t)s * 32 + lane, S, loc);
   }
+}
+
+// Second half of the cross items of the persistent interaction kernel: the sums
+// they left per slot (xcf [4][n_slices * 32]) into the targets' local expansions.
+__global__ void k_cross_apply(DevTree t, CrossCells xc, const double* __restrict__ xcf, double* __restrict__ loc) {
+  const int64_t n_slots = (int64_t)xc.n_slices * 32;
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= n_slots) return;
+  const double S[4] = {xcf[slot], xcf[n_slots + slot], xcf[2 * n_slots + slot], xcf[3 * n_slots + slot]};
+  cross::apply(t, xc, slot, S, loc);
 }
 
 // Adjoint of k_cross_cells (gather form).  Both directions of every pair are in
@@ -247,6 +219,14 @@ cudaError_t launch_cross_cells(const DevTree& t, const CrossCells& xc, const dou
   cudaError_t e = cudaMemsetAsync(xc.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_cross_cells<<<grid, kCrossCellsThreads, smem, s>>>(t, xc, mp, loc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cross_apply(const DevTree& t, const CrossCells& xc, const double* xcf, double* loc,
+                               cudaStream_t s) {
+  if (xc.n_slices == 0) return cudaSuccess;
+  const int64_t n_slots = (int64_t)xc.n_slices * 32;
+  k_cross_apply<<<(unsigned)((n_slots + 255) / 256), 256, 0, s>>>(t, xc, xcf, loc);
   return cudaGetLastError();
 }
 

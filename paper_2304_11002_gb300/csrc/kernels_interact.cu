@@ -10,6 +10,7 @@
 // The autotuner in capi.cu times both on the actual tree and keeps the faster.
 #include <algorithm>
 
+#include "cross.cuh"
 #include "items.cuh"
 
 namespace octo {
@@ -46,12 +47,15 @@ __global__ void __launch_bounds__(items::kThreads) k_near_items(DevTree t, const
 }
 
 // item = (node << 3) | (kind << 1) | half; kind 0 = interior (one half of the node),
-// 1 = leaf (the whole node), 2 = near field of a leaf node (mixed precision only)
+// 1 = leaf (the whole node), 2 = near field of a leaf node (mixed precision only),
+// 3 = kCrossSlicesPerItem slices of the tabulated cross-level pairs starting at
+// slice node * kCrossSlicesPerItem (sums per slot into xcf; k_cross_apply adds them
+// to the targets after the launch, so that no item writes what another one reads)
 template <bool MIXED, int MINB>
 __global__ void __launch_bounds__(items::kThreads, MINB)
     k_persistent(DevTree t, const int* __restrict__ queue, int n_items, int* __restrict__ counter, Stencils st,
                  const double* __restrict__ mp, const float* __restrict__ mp32, double* __restrict__ loc,
-                 double* __restrict__ nearf, int64_t NL) {
+                 double* __restrict__ nearf, int64_t NL, CrossCells xc, double* __restrict__ xcf) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next;
   for (;;) {
@@ -62,7 +66,20 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
     if (k >= n_items) return;
     const int it = queue[k];
     const int node = it >> 3, half = it & 1, kind = (it >> 1) & 3;
-    if (kind == 2) {
+    if (kind == 3) {
+      double2* tab2 = reinterpret_cast<double2*>(smem);
+      cross::stage_table(xc, tab2);
+      __syncthreads();
+      const int lane = threadIdx.x & 31;
+      const int s1 = min((node + 1) * kCrossSlicesPerItem, xc.n_slices);
+      const int64_t n_slots = (int64_t)xc.n_slices * 32;
+      for (int sl = node * kCrossSlicesPerItem + (threadIdx.x >> 5); sl < s1; sl += items::kThreads / 32) {
+        double S[4];
+        cross::slice_sums(xc, tab2, mp, sl, lane, S);
+        const int64_t slot = (int64_t)sl * 32 + lane;
+        for (int k = 0; k < 4; ++k) xcf[k * n_slots + slot] = S[k];
+      }
+    } else if (kind == 2) {
       if (MIXED) items::near_item(t, node, st, mp, nearf, NL, smem);
     } else if (kind == 1) {
       items::leaf_item<MIXED>(t, node, st, mp, mp32, loc, smem);
@@ -76,17 +93,17 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
 }
 
 // Dynamic shared memory of the persistent kernel: the largest of its item kinds
-// (float64 interior items use none).
-size_t persistent_smem_bytes(const Stencils& st, bool mixed) {
-  const size_t leaf = items::leaf_smem_bytes(st, mixed);
-  return mixed ? std::max({leaf, items::near_smem_bytes(st), items::interior_smem_bytes()}) : leaf;
+// (float64 interior items use none; cross items hold the cross kernel table).
+size_t persistent_smem_bytes(const Stencils& st, const CrossCells& xc, bool mixed) {
+  const size_t leaf = items::leaf_smem_bytes(st, mixed), cross = sizeof(double) * 4 * (size_t)xc.n_rows;
+  return std::max(cross, mixed ? std::max({leaf, items::near_smem_bytes(st), items::interior_smem_bytes()}) : leaf);
 }
 
 // Resident blocks per SM of a persistent variant (sets its shared-memory limit);
 // called once per handle, outside any stream capture.
 template <bool MIXED, int MINB>
-cudaError_t persistent_occupancy(const Stencils& st, int* per_sm) {
-  const size_t smem = persistent_smem_bytes(st, MIXED);
+cudaError_t persistent_occupancy(const Stencils& st, const CrossCells& xc, int* per_sm) {
+  const size_t smem = persistent_smem_bytes(st, xc, MIXED);
   cudaError_t e = cudaFuncSetAttribute(k_persistent<MIXED, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -97,11 +114,11 @@ cudaError_t persistent_occupancy(const Stencils& st, int* per_sm) {
 
 template <bool MIXED, int MINB>
 cudaError_t persistent_launch(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
-  const size_t smem = persistent_smem_bytes(a.st, MIXED);
+  const size_t smem = persistent_smem_bytes(a.st, a.xc, MIXED);
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_persistent<MIXED, MINB><<<a.grid, items::kThreads, smem, s>>>(t, a.queue, a.n_items, a.counter, a.st, a.mp,
-                                                                  a.mp32, a.loc, a.nearf, a.NL);
+                                                                  a.mp32, a.loc, a.nearf, a.NL, a.xc, a.xcf);
   return cudaGetLastError();
 }
 
@@ -160,13 +177,15 @@ cudaError_t launch_near_items(const DevTree& t, const InteractArgs& a, cudaStrea
 
 // Register budgets: 1 or 2 resident blocks per SM, and 3 in mixed precision (whose
 // items all fit 85 registers; the float64 interior item needs twice that).
-cudaError_t persistent_blocks_per_sm(bool mixed, int min_blocks, const Stencils& st, int* per_sm) {
+cudaError_t persistent_blocks_per_sm(bool mixed, int min_blocks, const Stencils& st, const CrossCells& xc,
+                                     int* per_sm) {
   if (mixed) {
-    if (min_blocks == 3) return persistent_occupancy<true, 3>(st, per_sm);
-    return min_blocks == 2 ? persistent_occupancy<true, 2>(st, per_sm) : persistent_occupancy<true, 1>(st, per_sm);
+    if (min_blocks == 3) return persistent_occupancy<true, 3>(st, xc, per_sm);
+    return min_blocks == 2 ? persistent_occupancy<true, 2>(st, xc, per_sm)
+                           : persistent_occupancy<true, 1>(st, xc, per_sm);
   }
   if (min_blocks == 3) return cudaErrorInvalidValue;
-  return min_blocks == 2 ? persistent_occupancy<false, 2>(st, per_sm) : persistent_occupancy<false, 1>(st, per_sm);
+  return min_blocks == 2 ? persistent_occupancy<false, 2>(st, xc, per_sm) : persistent_occupancy<false, 1>(st, xc, per_sm);
 }
 
 cudaError_t launch_persistent(const DevTree& t, const InteractArgs& a, cudaStream_t s) {

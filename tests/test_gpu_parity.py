@@ -99,7 +99,9 @@ def test_unbalanced_tree_full(precision):
     rho = np.random.default_rng(12).lognormal(size=(tree.n_leaf, 512))
     fmm, phi, g = _run(tree, rho, precision)
     names = _stage_names(fmm)
-    assert "cross_cells" in names and "cross_leaf" in names, names
+    # tabulated one-level pairs: their own stage (per-kind launches) or cross items of
+    # the persistent queue whose sums a short stage applies afterwards
+    assert any(n in ("cross_cells", "cross_cells_apply") for n in names) and "cross_leaf" in names, names
     po, go, _ = oracle.fmm(tree, rho)
     tol = TOL64 if precision == binding.OCTO_FP64 else 1e-6
     assert _rel_phi(phi, po) <= tol
