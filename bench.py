@@ -114,7 +114,8 @@ def dist_env():
 # roofline_traffic.json); it is reported only while the kernel sources are those the
 # capture was taken with (sha256 over these files), else null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-KERNEL_SOURCES = ("capi.cu", "device.cuh", "items.cuh", "kernels.h", "kernels_boundary.cu", "kernels_interact.cu")
+KERNEL_SOURCES = ("capi.cu", "cross.cuh", "device.cuh", "items.cuh", "kernels.h", "kernels_boundary.cu",
+                  "kernels_interact.cu")
 
 
 def kernel_sources_sha256():

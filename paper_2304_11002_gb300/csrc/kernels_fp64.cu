@@ -136,12 +136,16 @@ __global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_beg
 // (exact for the cubic Taylor polynomial), dg carried down unshifted.  At leaf
 // nodes the result is evaluated at the cell itself (L2P):
 //   phi = L0,  g = -L1 + dg  (plus the near-field sums when they are kept apart).
-__global__ void __launch_bounds__(256, 2) k_l2l(DevTree t, int node_begin, const double* __restrict__ mp,
-                                             double* __restrict__ loc, double* __restrict__ phi,
-                                             double* __restrict__ g, int64_t NL,
-                                             const double* __restrict__ nearf) {
-  const int node = node_begin + (blockIdx.x >> 1);
-  const int l = ((blockIdx.x & 1) << 8) + threadIdx.x;
+// One thread per cell, 128-thread blocks (four per node) with three resident per
+// SM: the polynomial shift keeps ~160 float64 registers live, which 256-thread
+// blocks at two per SM (128 registers) spilled.
+constexpr int kL2LThreads = 128;
+__global__ void __launch_bounds__(kL2LThreads, 3) k_l2l(DevTree t, int node_begin, const double* __restrict__ mp,
+                                                       double* __restrict__ loc, double* __restrict__ phi,
+                                                       double* __restrict__ g, int64_t NL,
+                                                       const double* __restrict__ nearf) {
+  const int node = node_begin + (blockIdx.x >> 2);
+  const int l = ((blockIdx.x & 3) * kL2LThreads) + threadIdx.x;
   const int64_t NC = t.NC;
   const int64_t cell = (int64_t)node * 512 + l;
   const bool leaf = t.children[8 * node] < 0;
@@ -238,7 +242,7 @@ cudaError_t launch_m2m(const DevTree& t, int b, int e, double* mp, float* mp32, 
 cudaError_t launch_l2l(const DevTree& t, int b, int e, const double* mp, double* loc, double* phi, double* g,
                        int64_t NL, const double* nearf, cudaStream_t s) {
   if (e <= b) return cudaSuccess;
-  k_l2l<<<2 * (e - b), 256, 0, s>>>(t, b, mp, loc, phi, g, NL, nearf);
+  k_l2l<<<(512 / kL2LThreads) * (e - b), kL2LThreads, 0, s>>>(t, b, mp, loc, phi, g, NL, nearf);
   return cudaGetLastError();
 }
 

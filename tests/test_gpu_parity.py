@@ -203,12 +203,19 @@ def test_interaction_strategies_bit_identical(precision):
     r = torch.from_numpy(w.rho.reshape(-1).copy()).cuda()
     outs = []
     budgets = (1, 2, 3) if precision == binding.OCTO_MIXED else (1, 2)
+    cross = None
     for mode, minb in [(1, 1)] + [(2, b) for b in budgets]:
         fmm = binding.OctoFMM(w.tree, 0.5, precision)
         binding.octo_fmm_set_option(fmm.handle, 3, mode)
         binding.octo_fmm_set_option(fmm.handle, 4, minb)
         phi, g = fmm.forces(r)
         outs.append((phi.clone(), g.clone()))
+        names = _stage_names(fmm)
+        if mode == 1:
+            cross = "cross_cells" in names
+        else:  # the tabulated cross-level pairs ran as items of the persistent queue
+            assert ("cross_cells_apply" in names) == cross, names
+    assert cross  # this tree has tabulated cross-level pairs
     for phi, g in outs[1:]:
         assert torch.equal(phi, outs[0][0]) and torch.equal(g, outs[0][1])
     fmm = binding.OctoFMM(w.tree, 0.5, precision)
