@@ -60,6 +60,9 @@ __global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_beg
   const int a = l & 7, b = (l >> 3) & 7, c = l >> 6;
   const int o = (a >> 2) + 2 * (b >> 2) + 4 * (c >> 2);
   const int ch = t.children[8 * node + o];
+  // a leaf child node's cells are point masses (P2M): their moments are zero, so
+  // they are not read (the same expressions then run on zeros)
+  const bool leaf_child = t.children[8 * ch] < 0;
   const int64_t NC = t.NC;
   // child cell e = ex + 2 ey + 4 ez of this parent cell
   const int64_t c0 = (int64_t)ch * 512 + 2 * (a & 3) + 8 * 2 * (b & 3) + 64 * 2 * (c & 3);
@@ -86,7 +89,9 @@ __global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_beg
     const double d1 = mp[(F_X + 1) * NC + ce] - X1;
     const double d2 = mp[(F_X + 2) * NC + ce] - X2;
     double q[6];
-    for (int i = 0; i < 6; ++i) q[i] = mp[(F_Q + i) * NC + ce];
+    for (int i = 0; i < 6; ++i) q[i] = leaf_child ? 0.0 : mp[(F_Q + i) * NC + ce];
+    double oc[10];
+    for (int i = 0; i < 10; ++i) oc[i] = leaf_child ? 0.0 : mp[(F_O + i) * NC + ce];
     const double md0 = mc * d0, md1 = mc * d1, md2 = mc * d2;
     Q[0] += q[0] + md0 * d0;
     Q[1] += q[1] + md0 * d1;
@@ -95,16 +100,16 @@ __global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_beg
     Q[4] += q[4] + md1 * d2;
     Q[5] += q[5] + md2 * d2;
     // 3 sym(q d)_abc = q_ab d_c + q_ac d_b + q_bc d_a
-    O[0] += mp[(F_O + 0) * NC + ce] + 3.0 * q[0] * d0 + md0 * d0 * d0;                    // xxx
-    O[1] += mp[(F_O + 1) * NC + ce] + q[0] * d1 + 2.0 * q[1] * d0 + md0 * d0 * d1;        // xxy
-    O[2] += mp[(F_O + 2) * NC + ce] + q[0] * d2 + 2.0 * q[2] * d0 + md0 * d0 * d2;        // xxz
-    O[3] += mp[(F_O + 3) * NC + ce] + 2.0 * q[1] * d1 + q[3] * d0 + md0 * d1 * d1;        // xyy
-    O[4] += mp[(F_O + 4) * NC + ce] + q[1] * d2 + q[2] * d1 + q[4] * d0 + md0 * d1 * d2;  // xyz
-    O[5] += mp[(F_O + 5) * NC + ce] + 2.0 * q[2] * d2 + q[5] * d0 + md0 * d2 * d2;        // xzz
-    O[6] += mp[(F_O + 6) * NC + ce] + 3.0 * q[3] * d1 + md1 * d1 * d1;                    // yyy
-    O[7] += mp[(F_O + 7) * NC + ce] + q[3] * d2 + 2.0 * q[4] * d1 + md1 * d1 * d2;        // yyz
-    O[8] += mp[(F_O + 8) * NC + ce] + 2.0 * q[4] * d2 + q[5] * d1 + md1 * d2 * d2;        // yzz
-    O[9] += mp[(F_O + 9) * NC + ce] + 3.0 * q[5] * d2 + md2 * d2 * d2;                    // zzz
+    O[0] += oc[0] + 3.0 * q[0] * d0 + md0 * d0 * d0;                    // xxx
+    O[1] += oc[1] + q[0] * d1 + 2.0 * q[1] * d0 + md0 * d0 * d1;        // xxy
+    O[2] += oc[2] + q[0] * d2 + 2.0 * q[2] * d0 + md0 * d0 * d2;        // xxz
+    O[3] += oc[3] + 2.0 * q[1] * d1 + q[3] * d0 + md0 * d1 * d1;        // xyy
+    O[4] += oc[4] + q[1] * d2 + q[2] * d1 + q[4] * d0 + md0 * d1 * d2;  // xyz
+    O[5] += oc[5] + 2.0 * q[2] * d2 + q[5] * d0 + md0 * d2 * d2;        // xzz
+    O[6] += oc[6] + 3.0 * q[3] * d1 + md1 * d1 * d1;                    // yyy
+    O[7] += oc[7] + q[3] * d2 + 2.0 * q[4] * d1 + md1 * d1 * d2;        // yyz
+    O[8] += oc[8] + 2.0 * q[4] * d2 + q[5] * d1 + md1 * d2 * d2;        // yzz
+    O[9] += oc[9] + 3.0 * q[5] * d2 + md2 * d2 * d2;                    // zzz
   }
   const int64_t pc = (int64_t)node * 512 + l;
   mp[pc] = m;
