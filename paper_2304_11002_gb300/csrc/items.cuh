@@ -442,23 +442,34 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
     for (int q = 0; q < 2; ++q)
 #pragma unroll
       for (int k = 0; k < 4; ++k) f[q][k] = 0.0f;
-    for (int s0i = 0; s0i < n_far; s0i += kAccBlock) {
-      const int s1i = min(s0i + kAccBlock, n_far);
+    // one stencil entry: the two cells' masses times the entry's kernel row
+    auto entry = [&](int s, float* pa, float* pb) {
+      const int off = __ldg(&far[s].x);
+      const float4 k = __ldg(fk + s);
+      const float m0 = halo32[lane_f + off], m1 = halo32[lane_f + off + dz];
+      pa[0] = fmaf(m0, k.x, pa[0]);
+      pa[1] = fmaf(m0, k.y, pa[1]);
+      pa[2] = fmaf(m0, k.z, pa[2]);
+      pa[3] = fmaf(m0, k.w, pa[3]);
+      pb[0] = fmaf(m1, k.x, pb[0]);
+      pb[1] = fmaf(m1, k.y, pb[1]);
+      pb[2] = fmaf(m1, k.z, pb[2]);
+      pb[3] = fmaf(m1, k.w, pb[3]);
+    };
+    // full blocks of kAccBlock entries fully unrolled (constant offsets into the
+    // tables, no per-entry loop control), then the last partial block
+    int s0i = 0;
+    for (; s0i + kAccBlock <= n_far; s0i += kAccBlock) {
+      float pa[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int u = 0; u < kAccBlock; ++u) entry(s0i + u, pa, pb);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f[0][k].add(pa[k]), f[1][k].add(pb[k]);
+    }
+    if (s0i < n_far) {
       float pa[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
-      for (int s = s0i; s < s1i; ++s) {
-        const int off = __ldg(&far[s].x);
-        const float4 k = __ldg(fk + s);
-        const float m0 = halo32[lane_f + off], m1 = halo32[lane_f + off + dz];
-        pa[0] = fmaf(m0, k.x, pa[0]);
-        pa[1] = fmaf(m0, k.y, pa[1]);
-        pa[2] = fmaf(m0, k.z, pa[2]);
-        pa[3] = fmaf(m0, k.w, pa[3]);
-        pb[0] = fmaf(m1, k.x, pb[0]);
-        pb[1] = fmaf(m1, k.y, pb[1]);
-        pb[2] = fmaf(m1, k.z, pb[2]);
-        pb[3] = fmaf(m1, k.w, pb[3]);
-      }
+      for (int s = s0i; s < n_far; ++s) entry(s, pa, pb);
 #pragma unroll
       for (int k = 0; k < 4; ++k) f[0][k].add(pa[k]), f[1][k].add(pb[k]);
     }

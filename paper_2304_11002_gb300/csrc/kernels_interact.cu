@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(items::kThreads, MIXED ? 3 : 1) k_interior_ite
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(items::kThreads) k_leaf_items(DevTree t, const int* __restrict__ nodes, Stencils st,
+__global__ void __launch_bounds__(items::kThreads, MIXED ? 3 : 1) k_leaf_items(DevTree t, const int* __restrict__ nodes, Stencils st,
                                                                  const double* __restrict__ mp,
                                                                  const float* __restrict__ mp32,
                                                                  double* __restrict__ loc) {
