@@ -111,19 +111,34 @@ def dist_env():
 
 
 # DRAM traffic of the roofline kernel comes from one ncu capture (profiles/
-# roofline_traffic.json); it is reported only while the kernel sources are those the
-# capture was taken with (sha256 over these files), else null.
+# roofline_traffic.json); it is reported only while the kernel code is that the
+# capture was taken with (sha256 over these files without their // comments and
+# blank lines), else null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 KERNEL_SOURCES = ("capi.cu", "cross.cuh", "device.cuh", "items.cuh", "kernels.h", "kernels_boundary.cu",
                   "kernels_interact.cu")
 
 
-def kernel_sources_sha256():
+def code_lines(text: str):
+    """The lines of a C++/CUDA source without // comments, trailing blanks and empty
+    lines (a comment edit leaves the compiled kernel, and so a capture, valid)."""
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            yield code
+
+
+def kernel_sources_sha256(read=None):
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2304_11002_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_2304_11002_gb300", "csrc", f)) as fh:
+                text = fh.read()
+        else:
+            text = read(f)
+        for code in code_lines(text):
+            h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 

@@ -3,10 +3,11 @@
 //  * per-kind launches: one grid over all interior items of every level, one grid
 //    over all leaf items;
 //  * persistent queue: one grid of (SMs x blocks per SM) blocks that pull items of
-//    both kinds, of every level, from a single atomic counter (largest items first),
-//    so that float32-heavy interior items and float64-heavy leaf items share the
-//    SMs and the tail of one kind overlaps the other.  The counter is reset by a
-//    memset issued before every launch; no block ever waits for another.
+//    every kind (interior, leaf far field, leaf near field, tabulated cross-level
+//    slices), of every level, from a single atomic counter, so that float32-heavy
+//    and float64-heavy items share the SMs and the tail of one kind overlaps the
+//    others.  The counter is reset by a memset issued before every launch; no block
+//    ever waits for another.
 // The autotuner in capi.cu times both on the actual tree and keeps the faster.
 #include <algorithm>
 
