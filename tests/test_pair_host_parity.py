@@ -1,0 +1,56 @@
+"""The solver's M2L pair expression (device.cuh, compiled here as host code, no GPU)
+against the oracle's M2L of one pair, element by element, on seeded records: a
+refined target (all 23 local-expansion values, octupole correction included) and
+a leaf target (L0, L1 and the correction of a point-mass target).  The solver
+writes the pair through radial factors and the oracle through the derivative
+tensors D0..D4, so the two agree only if every term, sign and index matches."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2304_11002_gb300", "csrc")
+
+
+def _records(rng, n, leaf_target):
+    A = np.zeros((n, 20))
+    B = np.zeros((n, 20))
+    for r in (A, B):
+        r[:, 0] = rng.uniform(0.5, 2.0, n)                 # mass
+        r[:, 4:10] = rng.normal(scale=0.3, size=(n, 6))    # raw second moments
+        r[:, 10:20] = rng.normal(scale=0.2, size=(n, 10))  # raw third moments
+    A[:, 1:4] = rng.normal(size=(n, 3))
+    # source 3-8 units away in a random direction
+    d = rng.normal(size=(n, 3))
+    d *= (rng.uniform(3.0, 8.0, n) / np.linalg.norm(d, axis=1))[:, None]
+    B[:, 1:4] = A[:, 1:4] + d
+    if leaf_target:
+        A[:, 4:] = 0.0
+    return A, B
+
+
+@pytest.mark.parametrize("leaf_target", [False, True])
+def test_pair_expression_matches_oracle(tmp_path, leaf_target):
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "pair_host_eval")
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-x", "cu", "-I", CSRC, os.path.join(HERE, "pair_host_eval.cu"),
+                    "-o", exe], check=True, capture_output=True, timeout=300)
+    rng = np.random.default_rng(17 + int(leaf_target))
+    A, B = _records(rng, 64, leaf_target)
+    lines = [" ".join([str(0 if leaf_target else 1)] + ["%.17g" % v for v in np.concatenate([a, b])])
+             for a, b in zip(A, B)]
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=300, check=True)
+    got = np.array([[float(v) for v in ln.split()] for ln in r.stdout.strip().splitlines()])
+    want = np.array([oracle.m2l_pair(a, b, correction=True) for a, b in zip(A, B)])
+    assert got.shape == want.shape == (64, 23)
+    cols = np.r_[0:4, 20:23] if leaf_target else np.arange(23)
+    scale = np.max(np.abs(want[:, cols]), axis=0)
+    err = np.max(np.abs(got[:, cols] - want[:, cols]), axis=0) / scale
+    assert np.all(err <= 1e-13), err
