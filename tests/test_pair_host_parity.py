@@ -34,23 +34,41 @@ def _records(rng, n, leaf_target):
     return A, B
 
 
-@pytest.mark.parametrize("leaf_target", [False, True])
-def test_pair_expression_matches_oracle(tmp_path, leaf_target):
+def _evaluate(tmp_path, flag, A, B):
     nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
     if nvcc is None:
         pytest.skip("nvcc not available")
     exe = str(tmp_path / "pair_host_eval")
     subprocess.run([nvcc, "-std=c++17", "-O2", "-x", "cu", "-I", CSRC, os.path.join(HERE, "pair_host_eval.cu"),
                     "-o", exe], check=True, capture_output=True, timeout=300)
+    lines = [" ".join([str(flag)] + ["%.17g" % v for v in np.concatenate([a, b])]) for a, b in zip(A, B)]
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=300, check=True)
+    return np.array([[float(v) for v in ln.split()] for ln in r.stdout.strip().splitlines()])
+
+
+@pytest.mark.parametrize("leaf_target", [False, True])
+def test_pair_expression_matches_oracle(tmp_path, leaf_target):
     rng = np.random.default_rng(17 + int(leaf_target))
     A, B = _records(rng, 64, leaf_target)
-    lines = [" ".join([str(0 if leaf_target else 1)] + ["%.17g" % v for v in np.concatenate([a, b])])
-             for a, b in zip(A, B)]
-    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=300, check=True)
-    got = np.array([[float(v) for v in ln.split()] for ln in r.stdout.strip().splitlines()])
+    got = _evaluate(tmp_path, 0 if leaf_target else 1, A, B)
     want = np.array([oracle.m2l_pair(a, b, correction=True) for a, b in zip(A, B)])
     assert got.shape == want.shape == (64, 23)
     cols = np.r_[0:4, 20:23] if leaf_target else np.arange(23)
     scale = np.max(np.abs(want[:, cols]), axis=0)
     err = np.max(np.abs(got[:, cols] - want[:, cols]), axis=0) / scale
     assert np.all(err <= 1e-13), err
+
+
+def test_float32_pair_expression_within_float32_rounding(tmp_path):
+    """The same expression in float32 on operands of order one (as the mixed far
+    field evaluates it, in cell-width units): one pair's error within 32 float32
+    rounding units (2^-24 each) of the largest value of every component; measured
+    below 1e-6.  (The mixed solve's 1e-6 bound applies to phi and g, sums over many
+    pairs.)"""
+    rng = np.random.default_rng(19)
+    A, B = _records(rng, 64, False)
+    got = _evaluate(tmp_path, 2, A, B)
+    want = np.array([oracle.m2l_pair(a, b, correction=True) for a, b in zip(A, B)])
+    err = np.max(np.abs(got - want), axis=0) / np.max(np.abs(want), axis=0)
+    assert np.all(err <= 32 * 2.0**-24), err
+    assert np.max(err) > 1e-12  # it did run in float32
