@@ -32,11 +32,28 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-interactions/s"
 L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
 
-# Peaks for the roofline (per GPU, at the 2070 MHz maximum SM clock of the recipe):
-#  float64: 1.25 TFLOP/s nominal -> 4 flop / clock / SM = 152 * 4 * 2.07e9
-#  float32: 128 lanes x 2 flop / clock / SM -> 152 * 256 * 2.07e9
+# Nominal peaks (per GPU, at the 2070 MHz maximum SM clock): float64 1.25 TFLOP/s
+# -> 4 flop / clock / SM = 152 * 4 * 2.07e9; float32 128 lanes x 2 flop / clock / SM
+# -> 152 * 256 * 2.07e9.  The roofline uses the peaks measured on the device by the
+# library's fused multiply-add probe (octo_fmm_measure_peak); these are the fallback.
 PEAK_FP64_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 PEAK_FP32_TFLOPS = 152 * 256 * 2.07e9 / 1e12
+NOMINAL_ALU = {"fp64": PEAK_FP64_TFLOPS, "fp32": PEAK_FP32_TFLOPS,
+               "source": "derived: 152 SMs x (4 fp64 | 256 fp32) flop/clk x 2.07 GHz"}
+
+
+def measure_alu_peaks(gpu_index: int, stream):
+    """float64 and float32 FMA rates of this GPU in TFLOP/s (the library's probe),
+    with the SM clocks sampled while the probe ran."""
+    from paper_2304_11002_gb300 import binding
+    with ClockSampler(gpu_index) as clk:
+        f64 = max(binding.octo_fmm_measure_peak(True, stream) for _ in range(2))
+        f32 = max(binding.octo_fmm_measure_peak(False, stream) for _ in range(2))
+    c = clk.summary()
+    return {"fp64": f64 / 1e12, "fp32": f32 / 1e12,
+            "source": f"measured: FMA-chain probe octo_fmm_measure_peak (best of 2 x 3 launches), "
+                      f"SM clock median {c['sm_mhz']} MHz of max {c['sm_max_mhz']}",
+            "clocks": c}
 
 
 def _measured_peaks():
@@ -115,8 +132,8 @@ def dist_env():
 # capture was taken with (sha256 over these files without their // comments and
 # blank lines), else null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-KERNEL_SOURCES = ("capi.cu", "cross.cuh", "device.cuh", "items.cuh", "kernels.h", "kernels_boundary.cu",
-                  "kernels_interact.cu")
+KERNEL_SOURCES = ("capi.cu", "cross.cuh", "device.cuh", "interact.cuh", "items.cuh", "kernels.h",
+                  "kernels_boundary.cu", "kernels_interact.cu", "kernels_interact_b64.cu", "tma.cuh")
 
 
 def code_lines(text: str):
@@ -167,56 +184,116 @@ def aggregate_over_ranks(t_rank_s: float, units_per_step: float, steps: int, ws:
     return units_per_step * steps * ws / t, t
 
 
-def cpu_baseline(w, seconds_target: float = 15.0, theta: float = 0.5):
-    """The oracle as it stands on the host cores, over a seeded sample of leaf cells
-    (the oracle evaluates the sample's interaction lists and those of its ancestors)."""
-    import oracle
-    nl = w.tree.n_leaf * 512
-    rng = np.random.default_rng(123)
-    n_probe = 64
-    idx = rng.choice(nl, size=min(n_probe, nl), replace=False)
-    mask = np.zeros(nl, np.uint8)
-    mask[idx] = 1
-    work = np.zeros(1, np.int64)
-    t0 = time.perf_counter()
-    oracle.fmm(w.tree, w.rho, theta, leaf_mask=mask, work=work)
-    dt = time.perf_counter() - t0
-    # scale the sample to about seconds_target of CPU work
-    n = int(min(nl, max(n_probe, n_probe * seconds_target / max(dt, 1e-3))))
-    idx = rng.choice(nl, size=n, replace=False)
-    mask[:] = 0
-    mask[idx] = 1
-    t0 = time.perf_counter()
-    oracle.fmm(w.tree, w.rho, theta, leaf_mask=mask, work=work)
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": float(work[0]) / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"{n} of {nl} leaf cells of {w.name} (their and their ancestors' interaction lists, "
-                      f"{int(work[0])} interactions, {dt:.1f} s, including the full upward pass)",
-            "seconds": dt}
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+class OracleSampler:
+    """The oracle as it stands, over seeded samples of leaf cells of a workload: it
+    evaluates the full upward pass, then the interaction lists of the sampled cells
+    and of their ancestors, and counts the ordered interactions it evaluated."""
+
+    def __init__(self, w, theta: float = 0.5, seed: int = 123):
+        import oracle
+        self.oracle = oracle
+        self.w, self.theta = w, theta
+        self.nl = w.tree.n_leaf * 512
+        self.rng = np.random.default_rng(seed)
+
+    def run(self, n_cells: int):
+        """(interactions evaluated, seconds) of one sample of n_cells leaf cells."""
+        n_cells = int(min(self.nl, max(1, n_cells)))
+        mask = np.zeros(self.nl, np.uint8)
+        mask[self.rng.choice(self.nl, size=n_cells, replace=False)] = 1
+        work = np.zeros(1, np.int64)
+        t0 = time.perf_counter()
+        self.oracle.fmm(self.w.tree, self.w.rho, self.theta, leaf_mask=mask, work=work)
+        return int(work[0]), time.perf_counter() - t0
+
+    def calibrate(self, seconds_target: float, n_probe: int = 64) -> int:
+        """Sample size that takes about seconds_target (the upward pass is a fixed cost
+        of every sample, so the size is scaled on the interaction part).  The probe
+        runs once per thread count."""
+        key = self.oracle.set_threads(0)
+        if getattr(self, "_probe", (None,))[0] != key:
+            _, t_fixed = self.run(1)
+            _, t_probe = self.run(n_probe)
+            self._probe = (key, t_fixed, max(t_probe - t_fixed, 1e-4) / n_probe)
+        _, t_fixed, per_cell = self._probe
+        return int(min(self.nl, max(n_probe, (seconds_target - t_fixed) / per_cell)))
+
+
+def cpu_baseline(w, seconds_target: float = 15.0, theta: float = 0.5, one_thread_seconds: float = 8.0):
+    """The oracle timed on the host cores (all of them, then one thread) over bounded
+    samples of the workload; value in ordered interactions per second."""
+    s = OracleSampler(w, theta)
+    threads = s.oracle.set_threads(0)
+    n = s.calibrate(seconds_target)
+    work, dt = s.run(n)
+    out = {"value": work / dt, "unit": METRIC, "cores": threads, "kind": "oracle",
+           "sample": f"{n} of {s.nl} leaf cells of {w.name} (their and their ancestors' interaction lists, "
+                     f"{work} interactions, {dt:.1f} s, including the full upward pass)",
+           "cpu_model": cpu_model(), "seconds": dt}
+    if one_thread_seconds > 0:
+        s.oracle.set_threads(1)
+        try:
+            n1 = s.calibrate(one_thread_seconds)
+            work1, dt1 = s.run(n1)
+        finally:
+            s.oracle.set_threads(threads)
+        out["one_thread"] = {"value": work1 / dt1, "cores": 1,
+                             "sample": f"{n1} leaf cells, {work1} interactions, {dt1:.1f} s"}
+    return out
 
 
 def run_reference(args):
+    """The oracle as the reference arm: every step is one bounded sample of the
+    workload (the warm-up steps short ones), timed on the host cores; ms_per_step is
+    the samples' own mean time and value their interactions per second."""
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
         return 0
     from paper_2304_11002_gb300 import workloads as W
     w = W.make(args.workload)
-    import oracle
-    oracle.lib()
-    per_step = []
-    cb = None
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(w, seconds_target=args.ref_seconds)
-        if i >= args.warmup:
-            per_step.append(cb["value"])
-    value = float(np.mean(per_step))
-    ms = 1e3 * counts_total(w) / value
+    s = OracleSampler(w, w.theta)
+    threads = s.oracle.set_threads(0)
+    per_step = min(args.ref_seconds, max(2.0, args.ref_budget / max(args.steps, 1)))
+    n_warm = s.calibrate(1.0)
+    n_step = s.calibrate(per_step)
+    for _ in range(args.warmup):
+        s.run(n_warm)
+    works, secs = [], []
+    for _ in range(args.steps):
+        wk, dt = s.run(n_step)
+        works.append(wk)
+        secs.append(dt)
+    value = float(np.sum(works)) / float(np.sum(secs))
+    sample = (f"{args.steps} samples of {n_step} of {s.nl} leaf cells of {w.name} (each: the full upward pass, "
+              f"then the sampled cells' and their ancestors' interaction lists; {int(np.mean(works))} "
+              f"interactions, {np.mean(secs):.1f} s per sample)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "note": w.note, "theta": w.theta, "order": 3},
-            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "note": w.note, "theta": w.theta, "order": 3,
+                       "step": "one bounded sample of the workload (see cpu_baseline.sample)"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -236,11 +313,17 @@ def counts_total(w):
 STRATEGY = {"auto": 0, "per-kind": 1, "persistent": 2}
 
 
-def time_solver(w, precision, steps, warmup, torch, flush, stream, strategy="auto", blocks=0):
+def time_solver(w, precision, steps, warmup, torch, flush, stream, strategy="auto", blocks=0, corr64=False,
+                shape=None):
     from paper_2304_11002_gb300 import binding
     fmm = binding.OctoFMM(w.tree, w.theta, precision)
     h = fmm.handle
     binding.octo_fmm_set_option(h, 2, 1)  # stage events inside the captured graph
+    if corr64:  # the float64-correction variant of the mixed path (per-kind launches)
+        binding.octo_fmm_set_option(h, 5, 1)
+    if shape and precision == binding.OCTO_MIXED:  # interior shape fixed instead of autotuned
+        binding.octo_fmm_set_option(h, 6, shape[0])
+        binding.octo_fmm_set_option(h, 7, shape[1])
     if strategy != "auto":
         binding.octo_fmm_set_option(h, 3, STRATEGY[strategy])
         if blocks:
@@ -268,8 +351,10 @@ def time_solver(w, precision, steps, warmup, torch, flush, stream, strategy="aut
     return fmm, info, np.array(step_ms), np.array(stage_ms), launches, (rho, phi, g)
 
 
-def roofline_of(info, mean_stage_ms, peaks):
-    """Roofline of the stage that takes longest (CUDA-event time per solve)."""
+def roofline_of(info, mean_stage_ms, peaks, alu=None):
+    """Roofline of the stage that takes longest (CUDA-event time per solve).  alu:
+    float64 / float32 peaks in TFLOP/s (default: the nominal ones)."""
+    alu = alu or NOMINAL_ALU
     k = int(np.argmax(mean_stage_ms))
     st = info[k]
     dur_s = mean_stage_ms[k] / 1e3
@@ -277,26 +362,27 @@ def roofline_of(info, mean_stage_ms, peaks):
         # A stage may mix float32 (far field) and float64 (near field) work: the
         # binding unit is the one whose work takes longer at its peak.
         f64, f32 = st["flops64"], st["flops"] - st["flops64"]
-        fp32_bound = f32 / PEAK_FP32_TFLOPS > f64 / PEAK_FP64_TFLOPS
-        peak = PEAK_FP32_TFLOPS if fp32_bound else PEAK_FP64_TFLOPS
+        fp32_bound = f32 / alu["fp32"] > f64 / alu["fp64"]
+        peak = alu["fp32"] if fp32_bound else alu["fp64"]
         achieved = (f32 if fp32_bound else f64) / dur_s / 1e12
         return {"bound": "alu", "kernel": st["name"], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "pipe": "fp32" if fp32_bound else "fp64",
-                "other_pipe_frac": ((f64 / dur_s / 1e12) / PEAK_FP64_TFLOPS if fp32_bound else
-                                    (f32 / dur_s / 1e12) / PEAK_FP32_TFLOPS),
-                "peak_source": ("derived: 152 SMs x %s x 2.07 GHz" % ("256 fp32 flop/clk" if fp32_bound else
-                                                                      "4 fp64 flop/clk (1.25 TFLOP/s nominal)"))}
+                "other_pipe_frac": ((f64 / dur_s / 1e12) / alu["fp64"] if fp32_bound else
+                                    (f32 / dur_s / 1e12) / alu["fp32"]),
+                "peak_source": alu["source"],
+                "peak_nominal": PEAK_FP32_TFLOPS if fp32_bound else PEAK_FP64_TFLOPS}
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = st["bytes"] / dur_s / 1e9
     return {"bound": "hbm", "kernel": st["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None, "peak_source": "measured" if peaks else "fallback"}
 
 
-def stage_rates(info, mean_stage_ms, peaks):
+def stage_rates(info, mean_stage_ms, peaks, alu=None):
     """Per stage: time, the float32 / float64 flop rates as fractions of their peaks,
     and for the tree passes also HBM GB/s as a fraction of the measured copy
     bandwidth (algorithmic bytes, every value read or written once)."""
+    alu = alu or NOMINAL_ALU
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     out = {}
     for i, st in enumerate(info):
@@ -307,8 +393,8 @@ def stage_rates(info, mean_stage_ms, peaks):
         if st["flops"] > 0:
             f64 = st["flops64"]
             f32 = st["flops"] - f64
-            d["fp32_frac"] = round(f32 / (ms / 1e3) / 1e12 / PEAK_FP32_TFLOPS, 4)
-            d["fp64_frac"] = round(f64 / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS, 4)
+            d["fp32_frac"] = round(f32 / (ms / 1e3) / 1e12 / alu["fp32"], 4)
+            d["fp64_frac"] = round(f64 / (ms / 1e3) / 1e12 / alu["fp64"], 4)
         if st["bytes"] > 0:
             gbs = st["bytes"] / (ms / 1e3) / 1e9
             d["gbs"] = round(gbs, 1)
@@ -317,12 +403,13 @@ def stage_rates(info, mean_stage_ms, peaks):
     return out
 
 
-def interaction_fp64_frac(info, mean_stage_ms):
+def interaction_fp64_frac(info, mean_stage_ms, alu=None):
     """float64 flop rate of all interaction stages together (their float64 flops over
     their summed event time) as a fraction of the float64 peak."""
+    alu = alu or NOMINAL_ALU
     f64 = sum(st["flops64"] for st in info if st["pairs"] > 0)
     ms = sum(float(mean_stage_ms[i]) for i, st in enumerate(info) if st["pairs"] > 0)
-    return f64 / (ms / 1e3) / 1e12 / PEAK_FP64_TFLOPS if ms > 0 else None
+    return f64 / (ms / 1e3) / 1e12 / alu["fp64"] if ms > 0 else None
 
 
 def run_ours(args):
@@ -341,6 +428,7 @@ def run_ours(args):
     precision = binding.OCTO_MIXED if args.precision == "mixed" else binding.OCTO_FP64
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    alu = NOMINAL_ALU if args.nominal_peaks else measure_alu_peaks(local, stream)
 
     def barrier():
         torch.cuda.synchronize()
@@ -350,7 +438,8 @@ def run_ours(args):
     barrier()
     with ClockSampler(local) as clk:
         fmm, info, step_ms, stage_ms, launches, bufs = time_solver(w, precision, args.steps, args.warmup, torch,
-                                                                   flush, stream, args.strategy, args.blocks)
+                                                                   flush, stream, args.strategy, args.blocks,
+                                                                   args.corr64, args.interior_shape)
     barrier()
     t_step = float(np.mean(step_ms))
 
@@ -364,7 +453,7 @@ def run_ours(args):
 
     # dominant kernel of the step and its roofline
     mean_stage = stage_ms.mean(axis=0)
-    roof = roofline_of(info, mean_stage, _measured_peaks())
+    roof = roofline_of(info, mean_stage, _measured_peaks(), alu)
     roof["traffic"], roof["traffic_source"] = recorded_traffic(roof["kernel"], w.name)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
@@ -391,7 +480,11 @@ def run_ours(args):
     strategy = {"chosen": {1: "per-kind launches", 2: "persistent work queue"}[gopt(3)],
                 "register_budget_blocks_per_sm": gopt(4),
                 "autotune_us": {"per_kind": gopt(10), "persistent_1": gopt(11), "persistent_2": gopt(12),
-                                "persistent_3": gopt(13)}}
+                                "persistent_3": gopt(13), "interior_chunk_64": gopt(14),
+                                "interior_quarter_node": gopt(15)}}
+    if precision == binding.OCTO_MIXED:
+        strategy["interior_shape"] = {"entries_per_float32_partial": gopt(6),
+                                      "items": {1: "half node", 2: "quarter node"}[gopt(7)]}
 
     if precision == binding.OCTO_MIXED and not args.no_fp64:
         del fmm
@@ -416,8 +509,8 @@ def run_ours(args):
         del fmm64, bufs64
         fp64 = {"value": n_inter / (float(np.mean(s_ms)) / 1e3), "ms_per_step": float(np.mean(s_ms)),
                 "stages_ms": {info64[i]["name"]: round(float(m64[i]), 4) for i in range(len(info64))},
-                "roofline": roofline_of(info64, m64, _measured_peaks()),
-                "interaction_fp64_frac": interaction_fp64_frac(info64, m64),
+                "roofline": roofline_of(info64, m64, _measured_peaks(), alu),
+                "interaction_fp64_frac": interaction_fp64_frac(info64, m64, alu),
                 "backward_ms": backward_ms}
 
     if rank != 0:
@@ -427,6 +520,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if precision == binding.OCTO_MIXED else "f64",
+        "mixed_correction": ("float64 (option 5)" if args.corr64 else "float32") if precision == binding.OCTO_MIXED
+        else None,
         "data": "synthetic",
         "config": {"workload": w.name, "note": w.note, "precision": args.precision, "theta": w.theta, "order": 3,
                    "n_leaf_subgrids": int(w.tree.n_leaf), "n_nodes": int(w.tree.n_nodes),
@@ -438,7 +533,9 @@ def run_ours(args):
         "roofline": roof,
         "interaction_strategy": strategy,
         "stages_ms": {info[i]["name"]: round(float(mean_stage[i]), 4) for i in range(len(info))},
-        "stage_rates": stage_rates(info, mean_stage, _measured_peaks()),
+        "stage_rates": stage_rates(info, mean_stage, _measured_peaks(), alu),
+        "alu_peaks_tflops": {"fp64": alu["fp64"], "fp32": alu["fp32"], "source": alu["source"],
+                             "nominal_fp64": PEAK_FP64_TFLOPS, "nominal_fp32": PEAK_FP32_TFLOPS},
         "e2e": e2e,
         "gpu_launches": int(launches * args.steps),
         "clocks": clocks,
@@ -448,7 +545,8 @@ def run_ours(args):
         line["mixed_over_fp64"] = value / ws / fp64["value"]
     if not args.no_cpu_baseline and ws == 1:
         cb = cpu_baseline(w, seconds_target=args.ref_seconds)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model",
+                                                   "one_thread")}
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -465,7 +563,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--interior-shape", type=int, nargs=2, metavar=("CHUNK", "SPLIT"), default=None,
+                    help="mixed precision: fix the interior shape (32|64 entries per float32 partial, "
+                         "1|2 = half|quarter-node items) instead of autotuning it")
+    ap.add_argument("--corr64", action="store_true",
+                    help="mixed precision with the angular-momentum correction in float64 (per-kind launches)")
+    ap.add_argument("--nominal-peaks", action="store_true",
+                    help="use the nominal float64/float32 peaks instead of measuring them on the device")
+    ap.add_argument("--ref-seconds", type=float, default=15.0,
+                    help="oracle seconds of the cpu_baseline sample and at most per reference step")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="oracle seconds of all timed reference steps together")
     ap.add_argument("--strategy", default="auto", choices=sorted(STRATEGY),
                     help="interaction phase: autotuned (default), per-kind launches or persistent queue")
     ap.add_argument("--blocks", type=int, default=0, choices=(0, 1, 2, 3),

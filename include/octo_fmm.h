@@ -19,8 +19,11 @@
  *    the 512 cells of a leaf are x-fastest (local = a + 8 b + 64 c).
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute calls are
  *    asynchronous: they enqueue work and return.  Launch and argument errors are
- *    returned immediately; errors detected on the device (bounded waits that ran
- *    out) are reported by the next call on the handle.
+ *    returned immediately.  Errors found on the device (a density that is not
+ *    finite and positive, a failed index check of the adjoint) are recorded in a
+ *    device word of the handle and reported, once, by the next octo_fmm_stats call
+ *    or by octo_fmm_forces_host, which read it back.  No kernel of this library
+ *    waits on another block, kernel or device.
  *  - Return value: OCTO_OK (0) or a negative OCTO_E* status; octo_fmm_last_error()
  *    gives a message.  No C++ exception crosses this interface.
  *  - One handle is not thread-safe; use one handle per host thread or serialise.
@@ -59,8 +62,8 @@ enum {
   OCTO_ETREE = -2,    /* inconsistent octree descriptor */
   OCTO_ENOMEM = -3,   /* device or host allocation failed */
   OCTO_ECUDA = -4,    /* a CUDA runtime call failed */
-  OCTO_ETIMEOUT = -5, /* a bounded device-side wait ran out */
-  OCTO_ENONPOS = -6,  /* reserved: non-positive density reported by a check */
+  OCTO_ETIMEOUT = -5, /* reserved: no call of this library waits on the device */
+  OCTO_ENONPOS = -6,  /* a leaf density was not finite and positive (NaN, <= 0, inf) */
   OCTO_ESTATE = -7    /* call out of order (e.g. backward before a forward solve) */
 };
 
@@ -71,6 +74,9 @@ enum {
 };
 
 /* Plans the solve and allocates the device workspace on the current device.
+ * Allocation failures return OCTO_ENOMEM and free everything allocated so far.
+ * (Test hook: with the environment variable OCTO_FMM_FAIL_ALLOC_AT=N set, the N-th
+ * device allocation of this call fails as if the device were out of memory.)
  * theta: opening parameter; cells A, B interact through their expansions iff
  *   theta |c_A - c_B| >= (sqrt 3 / 2)(h_A + h_B) for geometric centres c (inclusive,
  *   evaluated exactly).  Supported: 0.433 <= theta <= 1 (near field within the 26
@@ -82,7 +88,12 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
 
 /* Bottom-up traversal (Section VII-C, first phase): P2M at leaf cells (m = rho h^3
  * at the cell centre) and M2M level by level up to the root (moments about the
- * centre of mass, Section IV-C).  rho_dev: float64 [n_leaf*512], all entries > 0. */
+ * centre of mass, Section IV-C).  rho_dev: float64 [n_leaf*512], every entry finite
+ * and > 0 (centres of mass divide by the mass).  P2M checks this on the device: a
+ * violation leaves NaN or inf in the results and makes the next octo_fmm_stats (or
+ * octo_fmm_forces_host) return OCTO_ENONPOS.
+ * Starts a new solve: octo_fmm_backward accepts the state only after the matching
+ * octo_fmm_interact and octo_fmm_downward have followed. */
 int octo_fmm_upward(octo_fmm_t h, const double* rho_dev, void* stream);
 
 /* Same-level cell-to-cell interactions on every level (Section VII-C, second
@@ -102,7 +113,9 @@ int octo_fmm_forces(octo_fmm_t h, const double* rho_dev, double* phi_dev, double
 /* The same solve with HOST buffers (ordinary pageable memory is fine): copies rho
  * in and phi, g out on `stream` between the caller's buffers and device buffers
  * owned by the handle, and synchronises the stream before returning.
- * rho_host [n_leaf*512], phi_host [n_leaf*512], g_host [3][n_leaf*512]. */
+ * rho_host [n_leaf*512], phi_host [n_leaf*512], g_host [3][n_leaf*512].
+ * Returns OCTO_ENONPOS (results written, but not meaningful) if a density was not
+ * finite and positive. */
 int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host, double* g_host, void* stream);
 
 /* Vector-Jacobian product of the last forces/upward+interact+downward solve on this
@@ -113,8 +126,10 @@ int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host,
 int octo_fmm_backward(octo_fmm_t h, const double* dphi_dev, const double* dg_dev, double* drho_dev, void* stream);
 
 /* Ordered interaction counts of the plan: counts[0] same-level M2L, counts[1]
- * cross-level M2L, counts[2] same-level P2P, counts[3] cross-level P2P.  Also
- * reports a pending device-side error. */
+ * cross-level M2L, counts[2] same-level P2P, counts[3] cross-level P2P.
+ * Synchronises the device and reports a pending device-side error, then clears it:
+ * OCTO_ENONPOS for a density that was not finite and positive, OCTO_ECUDA for a
+ * failed index check of the adjoint (counts are filled in either case). */
 int octo_fmm_stats(octo_fmm_t h, int64_t counts[4]);
 
 /* Host-only planning: validates the tree and returns the counts above without
@@ -142,16 +157,31 @@ int octo_fmm_read_state(octo_fmm_t h, int which, double* host_out);
  *         is a separate item kind, interleaved with the float32 items so that
  *         both pipes of every SM work at once);
  *  key 4: register budget of the persistent launch: 1 or 2 resident blocks per SM,
- *         or 3 (mixed precision only).
+ *         or 3 (mixed precision only);
+ *  key 5: mixed precision only: precision of the angular-momentum correction terms
+ *         (Section IV-C) inside the float32 far-field pairs: 0 = float32 (default),
+ *         1 = float64, formed from the float64 multipoles and summed in float64
+ *         (a measurement variant; it runs as per-kind launches, key 3 = 1);
+ *  key 6: mixed precision: stencil entries per float32 partial sum of the interior
+ *         M2L items before its compensated merge: 32 (default) or 64;
+ *  key 7: mixed precision: interior items of half a node with one thread per target
+ *         cell (1, default), or of a quarter node with two threads per target cell,
+ *         each over one half of the stencil (2).
+ *  Keys 6 and 7 fix the interior shape; otherwise the autotuner chooses it (it
+ *  changes the float32 summation order, so results differ at float32 rounding).
  * Setting an option drops the captured graph.  Returns OCTO_EINVAL for an unknown
  * key or value. */
 int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value);
 
-/* Reads an option (keys 1-4 above; key 3 reports the strategy in use after
+/* Reads an option (keys 1-7 above; key 3 reports the strategy in use after
  * autotuning) or an autotuner measurement: keys 10, 11, 12, 13 = mean interaction
  * time in microseconds of per-kind launches and of the persistent launch with the
  * 1, 2 and 3 blocks/SM budgets; 0 when not measured (before autotuning, and key 13
- * in float64 mode). */
+ * in float64 mode); keys 14, 15 = mean interaction time in microseconds of the
+ * autotuner's shape candidates (chunk 64, quarter-node items; 0 when not
+ * measured).  Sizes of the handle (read-only): key 20 = leaf cells
+ * (n_leaf*512, the length of rho and phi), 21 = CUDA device the handle was created
+ * on, 22 = octree nodes, 23 = precision (OCTO_FP64 or OCTO_MIXED). */
 int octo_fmm_get_option(octo_fmm_t h, int key, int64_t* value);
 
 /* Number of kernel launches one octo_fmm_forces call enqueues. */
@@ -192,7 +222,10 @@ int octo_fmm_stage_times(octo_fmm_t h, float* ms, int cap);
  * No memory is allocated by this call: the only intermediate state (the cell
  * masses) lives in one fixed device array inside the library, sized for at most
  * 1024 subgrids (4 MiB), which every GPU that loads the library keeps until the
- * process exits.  n_subgrids outside [0, 1024] returns OCTO_EINVAL (message via
+ * process exits.  With CUDA's lazy module loading (the default) the driver
+ * reserves that array, and loads this code, at the first call on each device; so
+ * make one call (n_subgrids = 1 is enough) during set-up, and every later call
+ * allocates nothing.  n_subgrids outside [0, 1024] returns OCTO_EINVAL (message via
  * octo_fmm_last_error(NULL)) without launching anything.  The first call on a
  * device looks up that array's device address (once per device, with the device
  * current); make that first call before any stream capture.  Every call reuses
@@ -201,6 +234,16 @@ int octo_fmm_stage_times(octo_fmm_t h, float* ms, int cap);
  * them on one stream.  Asynchronous on `stream` like the other compute calls. */
 int octo_fmm_subgrids_noalloc(int n_subgrids, const double* rho_dev, double h, double* phi_dev, double* g_dev,
                               void* stream);
+
+/* Measured arithmetic peak of the current device, the denominator of the solver's
+ * roofline fractions (the paper has no counterpart; the interaction kernels are
+ * bound by the float64 and float32 fused multiply-add pipes, Section VII-C's
+ * "multipole kernel").  Runs independent fused multiply-add chains in float64
+ * (fp64 = 1) or float32 (fp64 = 0) on every SM, 3 timed launches of 20-50 ms after
+ * a warm-up, on `stream`, synchronises, and writes the rate in flop/s (an FMA
+ * counting 2) to *flops_per_s.  Allocates nothing.  Errors: OCTO_EINVAL, OCTO_ECUDA
+ * (message via octo_fmm_last_error(NULL)). */
+int octo_fmm_measure_peak(int fp64, double* flops_per_s, void* stream);
 
 /* Message for the last failing call on h (or for create failures, h = NULL). */
 const char* octo_fmm_last_error(octo_fmm_t h);

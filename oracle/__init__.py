@@ -54,6 +54,15 @@ def lib():
     return _LIB
 
 
+def set_threads(n: int = 0) -> int:
+    """Thread count of the oracle's OpenMP loops (n <= 0 leaves it); returns the
+    count in effect."""
+    L = lib()
+    L.oracle_set_threads.argtypes = [ctypes.c_int]
+    L.oracle_set_threads.restype = ctypes.c_int
+    return int(L.oracle_set_threads(int(n)))
+
+
 def _p(a, t):
     return a.ctypes.data_as(t) if a is not None else None
 

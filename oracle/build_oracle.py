@@ -1,7 +1,9 @@
 """Compile the CPU oracle (test infrastructure) into oracle/_build/liboracle.so.
 
-Plain g++, no fast-math, no FMA contraction, so the oracle's rounding is that of
-the written expressions.  Building the checker is not using it.
+Plain g++ at -O3, no fast-math, no FMA contraction, so the oracle's rounding is
+that of the written expressions.  No -march=native: the same flags build the same
+arithmetic on the x86 build host and on the Arm host of the GPU.  Building the
+checker is not using it.
 """
 import os
 import subprocess
@@ -15,9 +17,10 @@ OUT = os.path.join(OUT_DIR, "liboracle.so")
 
 def build(force: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= max(os.path.getmtime(SRC),
+                                                                           os.path.getmtime(__file__)):
         return OUT
-    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+    cmd = ["g++", "-std=c++17", "-O3", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
            "-shared", "-fPIC", "-o", OUT + ".tmp", SRC]
     subprocess.run(cmd, check=True)
     os.replace(OUT + ".tmp", OUT)

@@ -34,6 +34,9 @@
 #include <cstdint>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -1040,6 +1043,19 @@ void oracle_l2l(const double* parent, const double* delta, double* out) {
   zero(C);
   l2l(P, delta, C);
   pack_loc(C, out);
+}
+
+// Thread count of the OpenMP loops (timing of the oracle at 1 thread and at all
+// cores); returns the count now in effect.  No effect on any result: every loop
+// writes disjoint outputs.
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 }  // extern "C"

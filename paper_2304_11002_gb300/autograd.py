@@ -16,6 +16,9 @@ from . import binding
 class OctoFMMFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, rho: torch.Tensor, solver: "binding.OctoFMM"):
+        if rho.dtype != torch.float64 or rho.numel() != solver.n_leaf_cells or not rho.is_cuda:
+            raise ValueError(f"rho must be a float64 CUDA tensor of {solver.n_leaf_cells} elements "
+                             f"(got {rho.dtype}, {rho.numel()} elements, on {rho.device})")
         rho = rho.detach().contiguous()
         phi, g = solver.forces(rho)
         solver._forward_id = getattr(solver, "_forward_id", 0) + 1

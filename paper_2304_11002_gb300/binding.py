@@ -28,8 +28,8 @@ SYMBOLS = ["octo_fmm_create", "octo_fmm_upward", "octo_fmm_interact", "octo_fmm_
            "octo_fmm_forces_host", "octo_fmm_backward", "octo_fmm_stats", "octo_fmm_plan_counts",
            "octo_fmm_read_state", "octo_fmm_set_option", "octo_fmm_get_option", "octo_fmm_launches_per_solve",
            "octo_fmm_stage_count",
-           "octo_fmm_stage_info", "octo_fmm_stage_times", "octo_fmm_subgrids_noalloc", "octo_fmm_last_error",
-           "octo_fmm_destroy"]
+           "octo_fmm_stage_info", "octo_fmm_stage_times", "octo_fmm_subgrids_noalloc", "octo_fmm_measure_peak",
+           "octo_fmm_last_error", "octo_fmm_destroy"]
 
 
 class OctoError(RuntimeError):
@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
                                           i64p]
         L.octo_fmm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
         L.octo_fmm_subgrids_noalloc.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, vp]
+        L.octo_fmm_measure_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
         L.octo_fmm_last_error.argtypes = [vp]
         L.octo_fmm_last_error.restype = ctypes.c_char_p
         L.octo_fmm_destroy.argtypes = [vp]
@@ -105,12 +106,31 @@ class _Desc:
                              float(tree.extent))
 
 
-def _ptr(t) -> Optional[int]:
-    if t is None:
-        return None
-    if not (t.is_cuda and t.is_contiguous()):
-        raise ValueError("expected a contiguous CUDA tensor")
+def _buf(t, numel: int, device: Optional[int], name: str) -> int:
+    """Device address of a buffer the library reads or writes, after checking what the
+    kernels assume of it: a contiguous float64 CUDA tensor of exactly `numel`
+    elements on `device` (the handle's device).  A wrong size or dtype would make
+    the kernels read or write past the allocation, so it is refused here with a
+    ValueError before the library is called."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch CUDA tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor, got one on {t.device}")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name}: expected float64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name}: expected a tensor on cuda:{device} (the handle's device), got {t.device}")
     return t.data_ptr()
+
+
+def _sizes(h):
+    """(leaf cells, CUDA device) of handle h, as the library reports them."""
+    return octo_fmm_get_option(h, 20), octo_fmm_get_option(h, 21)
 
 
 def _stream(stream):
@@ -139,7 +159,8 @@ def octo_fmm_destroy(h) -> None:
 
 
 def octo_fmm_upward(h, rho, stream=None) -> None:
-    _check(lib().octo_fmm_upward(h, _ptr(rho), _stream(stream)), h)
+    n, dev = _sizes(h)
+    _check(lib().octo_fmm_upward(h, _buf(rho, n, dev, "rho"), _stream(stream)), h)
 
 
 def octo_fmm_interact(h, stream=None) -> None:
@@ -147,22 +168,30 @@ def octo_fmm_interact(h, stream=None) -> None:
 
 
 def octo_fmm_downward(h, phi, g, stream=None) -> None:
-    _check(lib().octo_fmm_downward(h, _ptr(phi), _ptr(g), _stream(stream)), h)
+    n, dev = _sizes(h)
+    _check(lib().octo_fmm_downward(h, _buf(phi, n, dev, "phi"), _buf(g, 3 * n, dev, "g"), _stream(stream)), h)
 
 
 def octo_fmm_forces(h, rho, phi, g, stream=None) -> None:
-    _check(lib().octo_fmm_forces(h, _ptr(rho), _ptr(phi), _ptr(g), _stream(stream)), h)
+    n, dev = _sizes(h)
+    _check(lib().octo_fmm_forces(h, _buf(rho, n, dev, "rho"), _buf(phi, n, dev, "phi"), _buf(g, 3 * n, dev, "g"),
+                                 _stream(stream)), h)
 
 
 def octo_fmm_forces_host(h, rho: np.ndarray, phi: np.ndarray, g: np.ndarray, stream=None) -> None:
-    for a in (rho, phi, g):
-        if not (a.dtype == np.float64 and a.flags.c_contiguous):
-            raise ValueError("host buffers must be contiguous float64")
+    n, _ = _sizes(h)
+    for name, a, k in (("rho", rho, n), ("phi", phi, n), ("g", g, 3 * n)):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise ValueError(f"{name}: host buffers must be contiguous float64 numpy arrays")
+        if a.size != k:
+            raise ValueError(f"{name}: expected {k} elements, got {a.size}")
     _check(lib().octo_fmm_forces_host(h, rho.ctypes.data, phi.ctypes.data, g.ctypes.data, _stream(stream)), h)
 
 
 def octo_fmm_backward(h, dphi, dg, drho, stream=None) -> None:
-    _check(lib().octo_fmm_backward(h, _ptr(dphi), _ptr(dg), _ptr(drho), _stream(stream)), h)
+    n, dev = _sizes(h)
+    _check(lib().octo_fmm_backward(h, _buf(dphi, n, dev, "dphi"), _buf(dg, 3 * n, dev, "dg"),
+                                   _buf(drho, n, dev, "drho"), _stream(stream)), h)
 
 
 def octo_fmm_stats(h) -> np.ndarray:
@@ -183,9 +212,22 @@ def octo_fmm_set_option(h, key: int, value: int) -> None:
 
 
 def octo_fmm_subgrids_noalloc(n_subgrids: int, rho, h: float, phi, g, stream=None) -> None:
-    """Allocation-free batch of single-subgrid solves (see include/octo_fmm.h)."""
-    _check(lib().octo_fmm_subgrids_noalloc(int(n_subgrids), _ptr(rho), float(h), _ptr(phi), _ptr(g),
-                                           _stream(stream)))
+    """Allocation-free batch of single-subgrid solves (see include/octo_fmm.h).  The
+    buffers must hold n_subgrids * 512 (g: 3 * n_subgrids * 512) float64 values on the
+    current CUDA device."""
+    import torch
+    n = max(int(n_subgrids), 0) * 512
+    dev = torch.cuda.current_device()
+    _check(lib().octo_fmm_subgrids_noalloc(int(n_subgrids), _buf(rho, n, dev, "rho"), float(h),
+                                           _buf(phi, n, dev, "phi"), _buf(g, 3 * n, dev, "g"), _stream(stream)))
+
+
+def octo_fmm_measure_peak(fp64: bool, stream=None) -> float:
+    """Measured float64 (fp64=True) or float32 fused multiply-add rate of the current
+    device in flop/s."""
+    v = ctypes.c_double()
+    _check(lib().octo_fmm_measure_peak(1 if fp64 else 0, ctypes.byref(v), _stream(stream)))
+    return float(v.value)
 
 
 def octo_fmm_get_option(h, key: int) -> int:

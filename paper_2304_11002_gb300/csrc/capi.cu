@@ -5,9 +5,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/octo_fmm.h"
@@ -30,11 +32,30 @@ void octo::set_global_error(const std::string& msg) {
 
 namespace {
 
+// Test hook for allocation failures: with OCTO_FMM_FAIL_ALLOC_AT=N in the
+// environment, the N-th device allocation (counting from 1) of an octo_fmm_create
+// call fails as if the device were out of memory.  Only create's allocations count;
+// the hook is read once at the start of every create call.
+thread_local int t_alloc_count = 0, t_alloc_fail_at = 0;
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (t_alloc_fail_at > 0 && ++t_alloc_count == t_alloc_fail_at) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+
 template <typename T>
 cudaError_t upload(T** dst, const std::vector<T>& src) {
   *dst = nullptr;
   if (src.empty()) return cudaSuccess;
-  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * src.size());
+  cudaError_t e = dev_malloc((void**)dst, sizeof(T) * src.size());
   if (e != cudaSuccess) return e;
   return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
 }
@@ -79,6 +100,12 @@ cudaError_t upload_cross(const Plan& P, const std::vector<int64_t>& targets, con
   return e;
 }
 
+// Work of the persistent queue's items, in any common unit: per M2L pair of an
+// interior item, per leaf node for the far-field item and for the near item.
+struct ItemCosts {
+  double interior_pair, leaf_far, leaf_near, cross_pair;
+};
+
 }  // namespace
 
 struct octo_fmm {
@@ -103,10 +130,14 @@ struct octo_fmm {
   CrossSet xg;
   // batched interaction phase: strategy (MODE_*), persistent work queue and counter
   int mode = 0, requested_mode = 0;
+  bool corr64 = false;  // mixed precision: correction terms in float64 (option 5)
+  int requested_shape = 0;  // 0: the autotuner picks the interior shape; 1: set by options 6 / 7
+  float tune_shape_ms[2] = {0, 0};  // autotune: chunk 64, quarter-node split
   int min_blocks = 1, n_sm = 0;
   int persist_per_sm[4] = {0, 0, 0, 0};  // resident blocks per SM of the persistent variants (index = budget)
-  int* d_queue = nullptr;
-  int n_items = 0;
+  int* d_queue = nullptr;  // sized for the largest queue (interior split 2)
+  int n_items = 0, queue_cap = 0;
+  ItemCosts costs{};  // item costs the queue is ordered by (estimates, then the autotuner's)
   int* d_counter = nullptr;
   int* d_err = nullptr;  // device-side check word of the adjoint kernels
   float tune_ms[4] = {0, 0, 0, 0};  // measured interaction time per strategy candidate (autotune)
@@ -122,10 +153,14 @@ struct octo_fmm {
   float* d_mp32 = nullptr;    // float32 multipoles (mixed precision only)
   double* d_near = nullptr;   // [4][leaf cells] near-field sums (mixed precision only)
   double* d_xcf = nullptr;    // [4][32 x cross slices] sums of the persistent kernel's cross items
-  float4* d_leaf_k32 = nullptr;  // mixed only: inline float32 kernel rows of the leaf far tables
+  uint4* d_leaf_blocks = nullptr;  // mixed only: the leaf far tables in 32-entry blocks (items.cuh)
   DevTree dt;
   Stencils st;
+  // Forward state for the adjoint: set once a whole solve has been enqueued (forces,
+  // or upward, interact and downward in that order); an upward or interact call
+  // starts a new solve and clears it until the solve is complete.
   bool forward_done = false;
+  int phase = 0;  // 1 after upward, 2 after upward + interact
   bool use_graph = true;
 
   // host-buffer path
@@ -175,7 +210,7 @@ void free_all(octo_fmm* h) {
                   h->d_bnd_index, h->d_mpb,    h->d_locb,
                   h->d_general,  h->d_queue,   h->d_counter, h->d_err,
                   h->d_leaf_far, h->d_leaf_root, h->d_leaf_near,
-                  h->d_leaf_k32};
+                  h->d_leaf_blocks};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int64_t* p : {h->xg.d_ft, h->xg.d_fs, h->xg.d_fm, h->xg.d_fsrc, h->xg.d_lt, h->xg.d_ls, h->xg.d_lm,
@@ -370,6 +405,7 @@ InteractArgs interact_args(const octo_fmm* h) {
   a.min_blocks = h->min_blocks;
   a.xc = h->xc;
   a.xcf = h->d_xcf;
+  a.corr64 = h->corr64;
   return a;
 }
 
@@ -377,7 +413,8 @@ cudaError_t enq_stage(octo_fmm* h, const octo_fmm::Stage& st, const double* rho,
                       cudaStream_t s) {
   const Plan& P = h->plan;
   switch (st.kind) {
-    case S_P2M: return launch_p2m(h->dt, h->d_leaf, (int)P.leaf_nodes.size(), rho, h->d_mp, h->d_mp32, s);
+    case S_P2M:
+      return launch_p2m(h->dt, h->d_leaf, (int)P.leaf_nodes.size(), rho, h->d_mp, h->d_mp32, h->d_err, s);
     case S_M2M: return launch_m2m(h->dt, st.a, st.b, h->d_mp, h->d_mp32, s);
     case S_M2L: return launch_interior_items(h->dt, interact_args(h), s);
     case S_CONV: return launch_leaf_items(h->dt, interact_args(h), s);
@@ -387,9 +424,9 @@ cudaError_t enq_stage(octo_fmm* h, const octo_fmm::Stage& st, const double* rho,
       if (h->mode == MODE_PERSISTENT) return launch_cross_apply(h->dt, h->xc, h->d_xcf, h->d_loc, s);
       return launch_cross_cells(h->dt, h->xc, h->d_mp, h->d_loc, h->xc_grid, s);
     case S_CROSS_FULL:
-      return launch_cross_list(h->dt, h->xg.f, true, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
+      return launch_cross_list(h->dt, h->xg.f, true, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s, h->corr64);
     case S_CROSS_LEAF:
-      return launch_cross_list(h->dt, h->xg.l, false, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s);
+      return launch_cross_list(h->dt, h->xg.l, false, h->d_mp, h->d_loc, h->precision == OCTO_MIXED, s, h->corr64);
     case S_L2L: return launch_l2l(h->dt, st.a, st.b, h->d_mp, h->d_loc, phi, g, h->n_leaf_cells(), h->d_near, s);
   }
   return cudaErrorInvalidValue;
@@ -454,12 +491,6 @@ std::vector<Kappa> make_kappa(int R) {
 
 namespace {
 
-// Work of the persistent queue's items, in any common unit: per M2L pair of an
-// interior item, per leaf node for the far-field item and for the near item.
-struct ItemCosts {
-  double interior_pair, leaf_far, leaf_near, cross_pair;
-};
-
 // Estimates before measurement, in SM cycles: an M2L pair with correction ~240
 // float32 instructions at 128 per cycle; a leaf node's far field ~1200 entries x 512
 // cells at ~24 instructions per pair (halo staging and boundary pairs included); its
@@ -470,25 +501,27 @@ ItemCosts default_costs(const Plan& P) {
           4.0 / 2.0 / 0.6};
 }
 
-// The persistent work queue (item = (node << 3) | (kind << 1) | half).  Interior
-// items (kind 0, one per half) of the root first (the largest), then of the other
-// levels; leaf items (kind 1, whole node) with refined neighbours before the
+// The persistent work queue (item = (node << 4) | (kind << 2) | part).  Interior
+// items (kind 0, one per half node, or per quarter with split 2) of the root first
+// (the largest), then of the other levels; leaf items (kind 1, whole node) with refined neighbours before the
 // others; cross items (kind 3, kCrossSlicesPerItem slices of the tabulated
 // cross-level pairs, widest first).  Float64: all interior items, then all leaf
 // items, then the cross items.  Mixed precision: the float32-bound items (interior,
 // leaf far field) and the float64-bound items (cross, then near items, kind 2) are
 // merged so that every prefix of the queue holds the same fraction of the work of
 // both, so that the two pipes of every SM stay busy side by side.
-std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c) {
+std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c, int split = 1) {
   std::vector<int32_t> q32, q64, q;
   std::vector<double> w32, w64;
-  auto item = [](int node, int kind, int half) { return (node << 3) | (kind << 1) | half; };
+  auto item = [](int node, int kind, int part) { return (node << 4) | (kind << 2) | part; };
+  const int parts = mixed ? 2 * split : 2;
   for (int pass = 0; pass < 2; ++pass)
     for (int k : P.interior_nodes)
       if ((P.level[k] == 0) == (pass == 0))
-        for (int half = 0; half < 2; ++half) {
-          q32.push_back(item(k, 0, half));
-          w32.push_back(256.0 * (P.level[k] == 0 ? (double)P.st_root.size() : (double)P.n_st) * c.interior_pair);
+        for (int part = 0; part < parts; ++part) {
+          q32.push_back(item(k, 0, part));
+          w32.push_back(512.0 / parts * (P.level[k] == 0 ? (double)P.st_root.size() : (double)P.n_st) *
+                        c.interior_pair);
         }
   const int n_slices = P.xc_slice_off.empty() ? 0 : (int)P.xc_slice_off.size() - 1;
   if (mixed)  // float64-bound: the cross items head the float64 list
@@ -531,31 +564,63 @@ std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c) 
   return q;
 }
 
+// (Re)builds the persistent queue for the handle's item costs and interior split
+// and copies it to the device, synchronising stream s.
+cudaError_t load_queue(octo_fmm* h, cudaStream_t s) {
+  const std::vector<int32_t> q = build_queue(h->plan, h->precision == OCTO_MIXED, h->costs, h->st.interior_split);
+  if ((int)q.size() > h->queue_cap) return cudaErrorInvalidValue;
+  h->n_items = (int)q.size();
+  if (q.empty()) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(h->d_queue, q.data(), sizeof(int32_t) * q.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
 // Mean time (ms) of one launch of the per-kind stage of `kind` (0 if the stage list
-// has none), over three launches on stream ts after a warm-up.
+// has none), over five launches on stream ts after a warm-up.
+constexpr int kTuneReps = 5;
 cudaError_t time_stage(octo_fmm* h, int kind, cudaStream_t ts, cudaEvent_t t0, cudaEvent_t t1, float* ms) {
   *ms = 0.0f;
   for (const auto& st : h->stages) {
     if (st.kind != kind) continue;
     cudaError_t e = enq_stage(h, st, nullptr, nullptr, nullptr, ts);
     if (e == cudaSuccess) e = cudaEventRecord(t0, ts);
-    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = enq_stage(h, st, nullptr, nullptr, nullptr, ts);
+    for (int r = 0; r < kTuneReps && e == cudaSuccess; ++r) e = enq_stage(h, st, nullptr, nullptr, nullptr, ts);
     if (e == cudaSuccess) e = cudaEventRecord(t1, ts);
     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, t0, t1);
-    *ms /= 3.0f;
+    *ms /= (float)kTuneReps;
     return e;
   }
   return cudaSuccess;
 }
 
-// Project autotuner of the batched interaction phase: after one upward pass with
-// this rho, times the interaction stages under each strategy (per-kind launches;
-// persistent queue with the 1-, 2- and, in mixed precision, 3-blocks-per-SM register
-// budgets) on the handle's own tree and keeps the fastest.  In mixed precision it
-// first times the three per-kind item stages alone and rebuilds the persistent
-// queue with the measured item costs.  Runs once per handle, on the private stream,
-// ordered after the caller's pending work.
+// Mean time (ms) of the whole interaction phase as the stage list stands, over five
+// runs after a warm-up.
+cudaError_t time_interact(octo_fmm* h, cudaStream_t ts, cudaEvent_t t0, cudaEvent_t t1, float* ms) {
+  *ms = 0.0f;
+  cudaError_t e = enq_interact(h, ts);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(t0, ts);
+  for (int r = 0; r < kTuneReps && e == cudaSuccess; ++r) e = enq_interact(h, ts);
+  if (e == cudaSuccess) e = cudaEventRecord(t1, ts);
+  if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, t0, t1);
+  *ms /= (float)kTuneReps;
+  return e;
+}
+
+// Project autotuner of the batched interaction phase, run once per handle on the
+// private stream (ordered after the caller's pending work) after one upward pass
+// with this rho, on the handle's own tree:
+//  1. mixed precision: times the item kinds alone (per-kind launches) and rebuilds
+//     the persistent queue with the measured item costs;
+//  2. schedule: per-kind launches, or the persistent queue under the 1-, 2- and (mixed
+//     precision) 3-blocks-per-SM register budgets; keeps the fastest;
+//  3. mixed precision, unless options 6 / 7 fixed it: the shape of the interior
+//     items under that schedule, one parameter at a time: the stencil entries per
+//     float32 partial sum (32, 64), then half-node or quarter-node items.
+// The schedule never changes the arithmetic (bit-identical results); the shape
+// changes the float32 summation order only (results within the mixed tolerance).
 int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
   cudaStream_t ts = h->cap_stream;
   cudaEvent_t ready = nullptr, t0 = nullptr, t1 = nullptr;
@@ -570,10 +635,11 @@ int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
   struct Cand {
     int mode, minb;
   } cands[4] = {{MODE_PER_KIND, 1}, {MODE_PERSISTENT, 1}, {MODE_PERSISTENT, 2}, {MODE_PERSISTENT, 3}};
-  const int n_cands = h->precision == OCTO_MIXED ? 4 : 3;  // budget 3: mixed precision only
+  const bool mixed = h->precision == OCTO_MIXED;
+  const int n_cands = mixed ? 4 : 3;  // budget 3: mixed precision only
   int best = 0;
-  if (e == cudaSuccess && h->precision == OCTO_MIXED && h->n_items > 0) {
-    // measured item costs -> persistent queue
+  if (e == cudaSuccess && mixed && h->n_items > 0) {
+    // 1. measured item costs -> persistent queue
     const Plan& P = h->plan;
     h->mode = MODE_PER_KIND;
     e = rebuild_stages(h);
@@ -587,37 +653,62 @@ int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
       const double cross_pair = t_cross > 0 && P.xc_pairs > 0
                                     ? t_cross / (double)P.xc_pairs
                                     : t_near / (double)P.n_leaf / default_costs(P).leaf_near * default_costs(P).cross_pair;
-      const ItemCosts c = {t_int / (double)P.kernel_pairs[0], t_far / (double)P.n_leaf, t_near / (double)P.n_leaf,
-                           cross_pair};
-      const std::vector<int32_t> q = build_queue(P, true, c);
-      if ((int)q.size() == h->n_items)
-        e = cudaMemcpyAsync(h->d_queue, q.data(), sizeof(int32_t) * q.size(), cudaMemcpyHostToDevice, ts);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+      h->costs = {t_int / (double)P.kernel_pairs[0], t_far / (double)P.n_leaf, t_near / (double)P.n_leaf, cross_pair};
+      e = load_queue(h, ts);
     }
   }
+  // 2. schedule
   for (int c = 0; c < n_cands && e == cudaSuccess; ++c) {
     h->mode = cands[c].mode;
     h->min_blocks = cands[c].minb;
     e = rebuild_stages(h);
-    if (e == cudaSuccess) e = enq_interact(h, ts);  // warm-up
-    if (e == cudaSuccess) e = cudaEventRecord(t0, ts);
-    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = enq_interact(h, ts);
-    if (e == cudaSuccess) e = cudaEventRecord(t1, ts);
-    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-    float ms = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-    h->tune_ms[c] = ms / 3.0f;
+    if (e == cudaSuccess) e = time_interact(h, ts, t0, t1, &h->tune_ms[c]);
     if (h->tune_ms[c] < h->tune_ms[best]) best = c;
+  }
+  if (e == cudaSuccess) {
+    h->mode = cands[best].mode;
+    h->min_blocks = cands[best].minb;
+    e = rebuild_stages(h);
+  }
+  // 3. interior shape (mixed precision)
+  if (e == cudaSuccess && mixed && !h->corr64 && h->requested_shape == 0 && !h->plan.interior_nodes.empty()) {
+    float t_best = h->tune_ms[best];
+    h->st.acc_block = 64;
+    e = time_interact(h, ts, t0, t1, &h->tune_shape_ms[0]);
+    if (e == cudaSuccess && h->tune_shape_ms[0] < t_best)
+      t_best = h->tune_shape_ms[0];
+    else
+      h->st.acc_block = 32;
+    if (e == cudaSuccess) {
+      h->st.interior_split = 2;
+      e = load_queue(h, ts);
+      if (e == cudaSuccess) e = time_interact(h, ts, t0, t1, &h->tune_shape_ms[1]);
+      if (e == cudaSuccess && !(h->tune_shape_ms[1] < t_best)) {
+        h->st.interior_split = 1;
+        e = load_queue(h, ts);
+      }
+    }
+    if (e == cudaSuccess) e = rebuild_stages(h);
   }
   h->profile = prof;
   if (ready) cudaEventDestroy(ready);
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);
   if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
-  h->mode = cands[best].mode;
-  h->min_blocks = cands[best].minb;
-  e = rebuild_stages(h);
-  return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "autotune");
+  return OCTO_OK;
+}
+
+// Reports the device error word read back as `err` (OCTO_ENONPOS for a density
+// that was not finite and positive, else OCTO_ECUDA for a failed index check of
+// the adjoint) and clears it, so that each error is reported once.
+int report_device_errors(octo_fmm* h, int err, cudaStream_t s) {
+  if (!err) return OCTO_OK;
+  cudaError_t e = cudaMemsetAsync(h->d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "clear the device error word");
+  if (err & kErrDensity)
+    return fail(h, OCTO_ENONPOS, "the density of a leaf cell was not finite and positive (NaN, <= 0 or inf)");
+  return fail(h, OCTO_ECUDA, "a device-side index check failed (bits " + std::to_string(err) + ")");
 }
 
 }  // namespace
@@ -645,6 +736,14 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   };
   if (!out) return create_fail(OCTO_EINVAL, "out is null");
   *out = nullptr;
+  {
+    const char* v = std::getenv("OCTO_FMM_FAIL_ALLOC_AT");
+    t_alloc_count = 0;
+    t_alloc_fail_at = v ? std::atoi(v) : 0;
+  }
+  struct DisarmHook {
+    ~DisarmHook() { t_alloc_fail_at = 0; }
+  } disarm_hook;
   if (order != 3) return create_fail(OCTO_EINVAL, "only order 3 is supported");
   if (precision != OCTO_FP64 && precision != OCTO_MIXED) return create_fail(OCTO_EINVAL, "unknown precision");
   octo_fmm* h = new (std::nothrow) octo_fmm();
@@ -685,19 +784,19 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   up(&h->d_xc_off, P.xc_slice_off);
   up(&h->d_xc_ent, P.xc_entries);
   up(&h->d_xc_tab, P.xc_table);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_xc_counter, sizeof(int));
+  if (e == cudaSuccess) e = dev_malloc(&h->d_xc_counter, sizeof(int));
   up(&h->d_cell_ent, P.cell_ent);
   up(&h->d_cell_ent_off, P.cell_ent_off);
   up(&h->d_bnd_perm, P.bnd_perm);
   up(&h->d_bnd_index, P.bnd_index);
   const int64_t NC = (int64_t)P.n_nodes * kCells;
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_mp, sizeof(double) * N_MP * NC);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_loc, sizeof(double) * N_LOC * NC);
-  if (e == cudaSuccess && precision == OCTO_MIXED) e = cudaMalloc(&h->d_mp32, sizeof(float) * N_MP * NC);
-  if (e == cudaSuccess && precision == OCTO_MIXED) e = cudaMalloc(&h->d_near, sizeof(double) * 4 * h->n_leaf_cells());
+  if (e == cudaSuccess) e = dev_malloc(&h->d_mp, sizeof(double) * N_MP * NC);
+  if (e == cudaSuccess) e = dev_malloc(&h->d_loc, sizeof(double) * N_LOC * NC);
+  if (e == cudaSuccess && precision == OCTO_MIXED) e = dev_malloc(&h->d_mp32, sizeof(float) * N_MP * NC);
+  if (e == cudaSuccess && precision == OCTO_MIXED) e = dev_malloc(&h->d_near, sizeof(double) * 4 * h->n_leaf_cells());
   if (e == cudaSuccess && P.xc_slice_off.size() > 1)
-    e = cudaMalloc(&h->d_xcf, sizeof(double) * 4 * 32 * (P.xc_slice_off.size() - 1));
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_io, sizeof(double) * 5 * h->n_leaf_cells());
+    e = dev_malloc(&h->d_xcf, sizeof(double) * 4 * 32 * (P.xc_slice_off.size() - 1));
+  if (e == cudaSuccess) e = dev_malloc(&h->d_io, sizeof(double) * 5 * h->n_leaf_cells());
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     std::string m = std::string("device setup failed: ") + cudaGetErrorString(e);
@@ -722,7 +821,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     t.h[l] = hl;
     t.h3[l] = hl * hl * hl;
   }
-  int RN = 0;
+  int RN = 0, far_blocks = 0, root_blocks = 0;
   for (int32_t v : P.st_near)
     for (int k = 0; k < 3; ++k) RN = std::max(RN, std::abs((int)(int8_t)((v >> (8 * k)) & 0xff)));
   {  // leaf-item tables (halo offsets and kernel rows per parity class and entry)
@@ -733,15 +832,28 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     e = upload(&h->d_leaf_far, lf);
     if (e == cudaSuccess) e = upload(&h->d_leaf_root, lr);
     if (e == cudaSuccess) e = upload(&h->d_leaf_near, ln);
-    if (precision == OCTO_MIXED) {  // float32 kernel rows inline: far entries, then root entries
-      std::vector<float4> k32;
-      k32.reserve(lf.size() + lr.size());
-      for (const std::vector<int2>* tab : {&lf, &lr})
-        for (const int2& en : *tab) {
-          const Kappa& v = kap[en.y];
-          k32.push_back(make_float4((float)v.v[0], (float)v.v[1], (float)v.v[2], (float)v.v[3]));
-        }
-      if (e == cudaSuccess) e = upload(&h->d_leaf_k32, k32);
+    if (precision == OCTO_MIXED) {
+      // blocks of 32 entries: 32 int32 halo offsets, then 32 float4 kernel rows
+      // (zero-padded past the end of a stencil); parity stencils, then level 0
+      far_blocks = (ns + kLeafBlock - 1) / kLeafBlock;
+      root_blocks = (nr + kLeafBlock - 1) / kLeafBlock;
+      constexpr int kWords = kLeafTableBlockBytes / 16;
+      std::vector<uint4> blk((size_t)8 * (far_blocks + root_blocks) * kWords, make_uint4(0, 0, 0, 0));
+      size_t b0 = 0;
+      for (auto [tab, n, nb] : {std::tuple{&lf, ns, far_blocks}, {&lr, nr, root_blocks}})
+        for (int p = 0; p < 8; ++p)
+          for (int bk = 0; bk < nb; ++bk, ++b0)
+            for (int u = 0; u < kLeafBlock; ++u) {
+              const int s_ = bk * kLeafBlock + u;
+              if (s_ >= n) break;
+              const int2 en = (*tab)[(size_t)p * n + s_];
+              const Kappa& v = kap[en.y];
+              unsigned char* base = reinterpret_cast<unsigned char*>(&blk[b0 * kWords]);
+              std::memcpy(base + 4 * u, &en.x, 4);
+              const float k4[4] = {(float)v.v[0], (float)v.v[1], (float)v.v[2], (float)v.v[3]};
+              std::memcpy(base + 4 * kLeafBlock + 16 * u, k4, 16);
+            }
+      if (e == cudaSuccess) e = upload(&h->d_leaf_blocks, blk);
     }
     if (e != cudaSuccess) {
       std::string m = std::string("device setup failed: ") + cudaGetErrorString(e);
@@ -751,8 +863,9 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     }
   }
   h->st = Stencils{h->d_st_parity, P.n_st,       h->d_st_root,   (int)P.st_root.size(), h->d_st_near,
-                   (int)P.st_near.size(), h->d_kappa, h->d_leaf_k32, R, RN, h->d_cell_ent, h->d_cell_ent_off,
-                   h->d_bnd_perm, h->d_bnd_index, h->d_leaf_far, h->d_leaf_root, h->d_leaf_near};
+                   (int)P.st_near.size(), h->d_kappa, h->d_leaf_blocks, far_blocks, root_blocks, R, RN,
+                   h->d_cell_ent, h->d_cell_ent_off, h->d_bnd_perm, h->d_bnd_index, h->d_leaf_far, h->d_leaf_root,
+                   h->d_leaf_near, h->d_err};
   h->xc = CrossCells{h->d_xc_t, h->d_xc_off, h->d_xc_ent, h->d_xc_tab, (int)(P.xc_slice_off.size() - 1),
                      (int)(P.xc_table.size() / 4), h->d_xc_counter};
   e = launch_init_leaf(t, h->d_leaf, (int)P.leaf_nodes.size(), h->d_mp, h->d_mp32, h->cap_stream);
@@ -766,12 +879,14 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   // persistent work queue (see build_queue); mixed precision: estimated item costs
   // until the autotuner has measured them
   {
-    const std::vector<int32_t> q = build_queue(P, precision == OCTO_MIXED, default_costs(P));
-    h->n_items = (int)q.size();
-    e = upload(&h->d_queue, q);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_counter, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
+    h->costs = default_costs(P);
+    h->queue_cap = (int)build_queue(P, precision == OCTO_MIXED, h->costs, precision == OCTO_MIXED ? 2 : 1).size();
+    e = h->queue_cap > 0 ? dev_malloc(&h->d_queue, sizeof(int32_t) * h->queue_cap) : cudaSuccess;
+    if (e == cudaSuccess) e = load_queue(h, h->cap_stream);
+    if (e == cudaSuccess) e = dev_malloc(&h->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc(&h->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+    h->st.err = h->d_err;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = configure_interact_kernels();
     for (int mb = 1; mb <= (precision == OCTO_MIXED ? 3 : 2) && e == cudaSuccess; ++mb)
@@ -783,7 +898,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
       std::string m = std::string("work queue setup failed: ") + cudaGetErrorString(e);
       free_all(h);
       delete h;
-      return create_fail(OCTO_ECUDA, m);
+      return create_fail(e == cudaErrorMemoryAllocation ? OCTO_ENOMEM : OCTO_ECUDA, m);
     }
   }
   h->mode = MODE_PER_KIND;  // until the autotuner (or option 3) decides
@@ -799,27 +914,40 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
 
 int octo_fmm_upward(octo_fmm_t h, const double* rho, void* stream) {
   if (!h || !rho) return h ? fail(h, OCTO_EINVAL, "rho is null") : OCTO_EINVAL;
+  h->forward_done = false;
+  h->phase = 0;
   cudaError_t e = enq_upward(h, rho, (cudaStream_t)stream);
-  return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "upward");
+  if (e != cudaSuccess) return cuda_fail(h, e, "upward");
+  h->phase = 1;
+  return OCTO_OK;
 }
 
 int octo_fmm_interact(octo_fmm_t h, void* stream) {
   if (!h) return OCTO_EINVAL;
+  h->forward_done = false;
+  const bool after_upward = h->phase == 1;
+  h->phase = 0;
   cudaError_t e = enq_interact(h, (cudaStream_t)stream);
-  return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "interact");
+  if (e != cudaSuccess) return cuda_fail(h, e, "interact");
+  if (after_upward) h->phase = 2;
+  return OCTO_OK;
 }
 
 int octo_fmm_downward(octo_fmm_t h, double* phi, double* g, void* stream) {
   if (!h || !phi || !g) return h ? fail(h, OCTO_EINVAL, "phi or g is null") : OCTO_EINVAL;
   cudaError_t e = enq_downward(h, phi, g, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "downward");
-  h->forward_done = true;
+  // the state is that of one whole solve only if upward and interact preceded this
+  if (h->phase == 2) h->forward_done = true;
+  h->phase = 0;
   return OCTO_OK;
 }
 
 int octo_fmm_forces(octo_fmm_t h, const double* rho, double* phi, double* g, void* stream) {
   if (!h || !rho || !phi || !g) return h ? fail(h, OCTO_EINVAL, "null buffer") : OCTO_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  h->forward_done = false;
+  h->phase = 0;
   if (h->requested_mode == MODE_AUTO && h->tune_ms[0] == 0.0f) {
     int rc = autotune(h, rho, s);
     if (rc != OCTO_OK) return rc;
@@ -877,9 +1005,11 @@ int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host,
   if (rc != OCTO_OK) return rc;
   e = cudaMemcpyAsync(phi_host, d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g_host, d_g, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "copy results out");
-  return OCTO_OK;
+  return report_device_errors(h, err, s);
 }
 
 int octo_fmm_backward(octo_fmm_t h, const double* dphi, const double* dg, double* drho, void* stream) {
@@ -936,10 +1066,10 @@ int octo_fmm_stats(octo_fmm_t h, int64_t counts[4]) {
   if (!h || !counts) return OCTO_EINVAL;
   for (int i = 0; i < 4; ++i) counts[i] = h->plan.counts[i];
   int err = 0;
-  cudaError_t e = cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(h, e, "stats");
-  if (err) return fail(h, OCTO_ECUDA, "a device-side index check failed (bits " + std::to_string(err) + ")");
-  return OCTO_OK;
+  return report_device_errors(h, err, nullptr);
 }
 
 int octo_fmm_read_state(octo_fmm_t h, int which, double* out) {
@@ -972,7 +1102,34 @@ int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value) {
     return OCTO_OK;
   }
   if (key == 0 && value >= 0) return OCTO_OK;
+  if (key == 5 && (value == 0 || value == 1) && h->precision == OCTO_MIXED) {
+    // the float64-correction variant runs as per-kind launches of half-node items
+    h->corr64 = value != 0;
+    cudaError_t e = cudaSuccess;
+    if (h->corr64) {
+      h->requested_mode = h->mode = MODE_PER_KIND;
+      h->st.interior_split = 1;
+      e = load_queue(h, h->cap_stream);
+    }
+    if (e == cudaSuccess) e = rebuild_stages(h);
+    return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "set correction precision");
+  }
+  if (key == 6 && (value == 32 || value == 64)) {
+    h->st.acc_block = (int)value;
+    h->requested_shape = 1;
+    cudaError_t e = rebuild_stages(h);
+    return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "set chunk length");
+  }
+  if (key == 7 && (value == 1 || (value == 2 && h->precision == OCTO_MIXED && !h->corr64))) {
+    h->st.interior_split = (int)value;
+    h->requested_shape = 1;
+    cudaError_t e = load_queue(h, h->cap_stream);
+    if (e == cudaSuccess) e = rebuild_stages(h);
+    return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "set interior split");
+  }
   if (key == 3 && value >= MODE_AUTO && value <= MODE_PERSISTENT) {
+    if (h->corr64 && value != MODE_PER_KIND)
+      return fail(h, OCTO_EINVAL, "the float64-correction variant runs as per-kind launches only");
     h->requested_mode = (int)value;
     if (value != MODE_AUTO) h->mode = (int)value;
     cudaError_t e = rebuild_stages(h);
@@ -1029,10 +1186,19 @@ int octo_fmm_get_option(octo_fmm_t h, int key, int64_t* value) {
     case 2: *value = h->profile ? 1 : 0; return OCTO_OK;
     case 3: *value = h->mode; return OCTO_OK;
     case 4: *value = h->min_blocks; return OCTO_OK;
+    case 5: *value = h->corr64 ? 1 : 0; return OCTO_OK;
+    case 6: *value = h->st.acc_block; return OCTO_OK;
+    case 7: *value = h->st.interior_split; return OCTO_OK;
+    case 14:
+    case 15: *value = (int64_t)(1000.0f * h->tune_shape_ms[key - 14]); return OCTO_OK;
     case 10:
     case 11:
     case 12:
     case 13: *value = (int64_t)(1000.0f * h->tune_ms[key - 10]); return OCTO_OK;
+    case 20: *value = h->n_leaf_cells(); return OCTO_OK;
+    case 21: *value = h->device; return OCTO_OK;
+    case 22: *value = h->plan.n_nodes; return OCTO_OK;
+    case 23: *value = h->precision; return OCTO_OK;
   }
   return fail(h, OCTO_EINVAL, "unknown option");
 }

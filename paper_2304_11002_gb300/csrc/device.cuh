@@ -15,6 +15,13 @@ constexpr int F_M = 0, F_X = 1, F_Q = 4, F_O = 10;          // multipole field o
 constexpr int G_L0 = 0, G_L1 = 1, G_L2 = 4, G_L3 = 10, G_DG = 20;  // local-expansion offsets
 constexpr int N_MP = 20, N_LOC = 23;
 
+// Bits of the handle's device error word.  The adjoint's index checks use the low
+// bits (see kernels_adjoint.cu); P2M sets kErrDensity for a density that is not
+// finite and positive; kErrTimeout is set when a kernel's bounded wait for its own
+// asynchronous copies ran out (the item's results are then incomplete).
+constexpr int kErrDensity = 1 << 30;
+constexpr int kErrTimeout = 1 << 29;
+
 struct DevTree {
   int64_t NC;  // number of cells = n_nodes * 512
   int n_nodes;
@@ -116,6 +123,51 @@ __host__ __device__ __forceinline__ void acc_zero(A& a) {
   a.W = 0;
 }
 
+// Angular-momentum correction of one far pair (target A, source B, R = X_A - X_B):
+//   dg_A += (m_B O_A - m_A O_B):D4 / (6 m_A),
+// written with Oh = O_A / m_A as ((m_B Oh - O_B):D4)/6 and, for a 3-tensor C,
+//   (C:D4)_a = f4 R_a (C:RRR) + 3 f3 [(C.RR)_a + R_a (tC.R)] + 3 f2 tC_a,  tC_a = C_abb,
+// from the source octupole's contractions with R (u = O_B.RR, sB = O_B:RRR, its
+// trace vector t and tauB = t.R; the M2L terms use them too).  TOCT: the target
+// has an octupole (interior cell); otherwise Oh = 0.
+template <bool TOCT, typename T, typename A>
+__host__ __device__ __forceinline__ void corr_pair(const T R0, const T R1, const T R2, const T m, const T xx,
+                                                   const T xy2, const T xz2, const T yy, const T yz2, const T zz,
+                                                   const T u0, const T u1, const T u2, const T sB, const T t0,
+                                                   const T t1, const T t2, const T tauB, const T* Oh, const T* tOh,
+                                                   const T f2, const T f3, const T f4, A& a) {
+  T cS, cT, v0, v1, v2, w0, w1, w2;
+  if constexpr (TOCT) {
+    const T uA0 = Oh[0] * xx + Oh[1] * xy2 + Oh[2] * xz2 + Oh[3] * yy + Oh[4] * yz2 + Oh[5] * zz;
+    const T uA1 = Oh[1] * xx + Oh[3] * xy2 + Oh[4] * xz2 + Oh[6] * yy + Oh[7] * yz2 + Oh[8] * zz;
+    const T uA2 = Oh[2] * xx + Oh[4] * xy2 + Oh[5] * xz2 + Oh[7] * yy + Oh[8] * yz2 + Oh[9] * zz;
+    const T sA = uA0 * R0 + uA1 * R1 + uA2 * R2;
+    const T tauA = tOh[0] * R0 + tOh[1] * R1 + tOh[2] * R2;
+    cS = m * sA - sB;
+    cT = m * tauA - tauB;
+    v0 = m * uA0 - u0;
+    v1 = m * uA1 - u1;
+    v2 = m * uA2 - u2;
+    w0 = m * tOh[0] - t0;
+    w1 = m * tOh[1] - t1;
+    w2 = m * tOh[2] - t2;
+  } else {
+    cS = -sB;
+    cT = -tauB;
+    v0 = -u0;
+    v1 = -u1;
+    v2 = -u2;
+    w0 = -t0;
+    w1 = -t1;
+    w2 = -t2;
+  }
+  const T kR = f4 * cS * (T)(1.0 / 6.0) + (T)0.5 * f3 * cT;
+  const T k3 = (T)0.5 * f3, k2 = (T)0.5 * f2;
+  a.dg[0] += kR * R0 + k3 * v0 + k2 * w0;
+  a.dg[1] += kR * R1 + k3 * v1 + k2 * w1;
+  a.dg[2] += kR * R2 + k3 * v2 + k2 * w2;
+}
+
 // One M2L contribution of source B (m, quadrupole Q, octupole O, all about its
 // centre of mass) to target A, with R = X_A - X_B.  Truncation n + k <= 3:
 //   L0  += -[ m D0 + Q:D2/2 - O:D3/6 ]
@@ -123,12 +175,11 @@ __host__ __device__ __forceinline__ void acc_zero(A& a) {
 //   L2  += -m D2,   L3 += -m D3
 // with D^(n) = grad^n (1/|R|) written through the radial factors
 // f0 = 1/r, f_{n+1} = -(2n+1) f_n / r^2:
-//   D1 = f1 R, D2 = f2 RR + f1 I, D3 = f3 RRR + f2 (I R)_sym, D4 = f4 RRRR + f3 (I RR)_sym + f2 (I I)_sym.
-// Angular-momentum correction: dg_A += (m_B O_A - m_A O_B):D4 / (6 m_A), written with
-// Oh = O_A / m_A as ((m_B Oh - O_B):D4)/6 and, for a 3-tensor C,
-//   (C:D4)_a = f4 R_a (C:RRR) + 3 f3 [(C.RR)_a + R_a (tC.R)] + 3 f2 tC_a,  tC_a = C_abb.
+//   D1 = f1 R, D2 = f2 RR + f1 I, D3 = f3 RRR + f2 (I R)_sym, D4 = f4 RRRR + f3 (I RR)_sym + f2 (I I)_sym,
+// plus the angular-momentum correction (corr_pair) unless CORR is false (the
+// caller then forms it separately, in float64).
 // FULL: the target needs L2/L3 (interior cell).  TOCT: the target has an octupole.
-template <bool FULL, bool TOCT, typename T, typename A>
+template <bool FULL, bool TOCT, typename T, typename A, bool CORR = true>
 __host__ __device__ __forceinline__ void m2l_pair(const T R0, const T R1, const T R2, const T m, const T* Q, const T* O,
                                                   const T* Oh, const T* tOh, T rinv, A& a) {
   const T ir2 = rinv * rinv;
@@ -184,37 +235,36 @@ __host__ __device__ __forceinline__ void m2l_pair(const T R0, const T R1, const 
     a.V[1] += mf2 * R1;
     a.V[2] += mf2 * R2;
   }
-  // correction with C = m Oh - O
-  T cS, cT, v0, v1, v2, w0, w1, w2;
-  if constexpr (TOCT) {
-    const T uA0 = Oh[0] * xx + Oh[1] * xy2 + Oh[2] * xz2 + Oh[3] * yy + Oh[4] * yz2 + Oh[5] * zz;
-    const T uA1 = Oh[1] * xx + Oh[3] * xy2 + Oh[4] * xz2 + Oh[6] * yy + Oh[7] * yz2 + Oh[8] * zz;
-    const T uA2 = Oh[2] * xx + Oh[4] * xy2 + Oh[5] * xz2 + Oh[7] * yy + Oh[8] * yz2 + Oh[9] * zz;
-    const T sA = uA0 * R0 + uA1 * R1 + uA2 * R2;
-    const T tauA = tOh[0] * R0 + tOh[1] * R1 + tOh[2] * R2;
-    cS = m * sA - sB;
-    cT = m * tauA - tauB;
-    v0 = m * uA0 - u0;
-    v1 = m * uA1 - u1;
-    v2 = m * uA2 - u2;
-    w0 = m * tOh[0] - t0;
-    w1 = m * tOh[1] - t1;
-    w2 = m * tOh[2] - t2;
-  } else {
-    cS = -sB;
-    cT = -tauB;
-    v0 = -u0;
-    v1 = -u1;
-    v2 = -u2;
-    w0 = -t0;
-    w1 = -t1;
-    w2 = -t2;
-  }
-  const T kR = f4 * cS * (T)(1.0 / 6.0) + (T)0.5 * f3 * cT;
-  const T k3 = (T)0.5 * f3, k2 = (T)0.5 * f2;
-  a.dg[0] += kR * R0 + k3 * v0 + k2 * w0;
-  a.dg[1] += kR * R1 + k3 * v1 + k2 * w1;
-  a.dg[2] += kR * R2 + k3 * v2 + k2 * w2;
+  if constexpr (CORR)
+    corr_pair<TOCT>(R0, R1, R2, m, xx, xy2, xz2, yy, yz2, zz, u0, u1, u2, sB, t0, t1, t2, tauB, Oh, tOh, f2, f3, f4, a);
+}
+
+// Float64 accumulator of the correction alone (float64-correction variant of the
+// mixed path).
+struct DgAcc {
+  double dg[3];
+};
+
+// The angular-momentum correction of one far pair on its own, in float64 from the
+// float64 multipoles: R = X_A - X_B, source mass m and octupole O, target Oh = O_A /
+// m_A and its trace vector tOh (TOCT), 1/|R| = rinv.
+template <bool TOCT>
+__host__ __device__ __forceinline__ void corr_pair_f64(const double R0, const double R1, const double R2,
+                                                       const double m, const double* O, const double* Oh,
+                                                       const double* tOh, const double rinv, DgAcc& a) {
+  const double ir2 = rinv * rinv;
+  const double f2 = 3.0 * rinv * ir2 * ir2;
+  const double f3 = -5.0 * f2 * ir2;
+  const double f4 = -7.0 * f3 * ir2;
+  const double xx = R0 * R0, xy = R0 * R1, xz = R0 * R2, yy = R1 * R1, yz = R1 * R2, zz = R2 * R2;
+  const double xy2 = xy + xy, xz2 = xz + xz, yz2 = yz + yz;
+  const double u0 = O[0] * xx + O[1] * xy2 + O[2] * xz2 + O[3] * yy + O[4] * yz2 + O[5] * zz;
+  const double u1 = O[1] * xx + O[3] * xy2 + O[4] * xz2 + O[6] * yy + O[7] * yz2 + O[8] * zz;
+  const double u2 = O[2] * xx + O[4] * xy2 + O[5] * xz2 + O[7] * yy + O[8] * yz2 + O[9] * zz;
+  const double sB = u0 * R0 + u1 * R1 + u2 * R2;
+  const double t0 = O[0] + O[3] + O[5], t1 = O[1] + O[6] + O[8], t2 = O[2] + O[7] + O[9];
+  const double tauB = t0 * R0 + t1 * R1 + t2 * R2;
+  corr_pair<TOCT>(R0, R1, R2, m, xx, xy2, xz2, yy, yz2, zz, u0, u1, u2, sB, t0, t1, t2, tauB, Oh, tOh, f2, f3, f4, a);
 }
 
 // Adds the deferred Kronecker-delta parts into L2 / L3.

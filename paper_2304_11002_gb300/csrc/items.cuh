@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace octo {
 namespace items {
@@ -84,8 +85,8 @@ __device__ __forceinline__ void interior_f64(const DevTree& t, int node, int hal
 
 // ------------------------------------------------------------ interior, float32
 // Positions relative to node centres in cell widths: R = x_A - (x_B + 8 o) for a
-// source in neighbour slot o.  Accumulation: the pair terms of kAccBlock stencil
-// entries are summed in plain float32 (fused multiply-adds); each partial sum then
+// source in neighbour slot o.  Accumulation: the pair terms of st.acc_block (16, 32
+// or 64; 32 by default) stencil entries are summed in plain float32 (fused multiply-adds); each partial sum then
 // gets its deferred Kronecker parts (acc_finish is linear) and is added by an
 // error-free transformation (TwoSum) into a float32 (sum, compensation) pair per
 // field, kept in shared memory; sum + compensation is converted to float64 once, at
@@ -95,7 +96,6 @@ __device__ __forceinline__ void interior_f64(const DevTree& t, int node, int hal
 // float32 sum at about a fifth of the instructions, with no float64 arithmetic
 // inside the loop (the float64 pipe stays free for the near-field items that share
 // the SM) and the 27 partials as the only accumulator registers.
-constexpr int kAccBlock = 32;
 constexpr int kInteriorFields = N_LOC;
 
 // Shared memory of an interior item: one float2 (sum, compensation) per field and
@@ -133,14 +133,60 @@ __device__ __forceinline__ void load_mp32(const float* __restrict__ mp32, int64_
   O[6] = v4.x, O[7] = v4.y, O[8] = v4.z, O[9] = v4.w;
 }
 
-__device__ __forceinline__ void interior_f32(const DevTree& t, int node, int half, const Stencils& st,
+// Target cell and stencil range of a thread of an interior item.  split 1: part =
+// half (0, 1) of the node, thread = cell (cell_of), all entries.  split 2: part =
+// quarter (0..3) of the node = parity classes 2 part and 2 part + 1 (warps 0-3 and
+// 4-7 hold the same 128 cells, one stencil half each); still one parity class per
+// warp.
+__host__ __device__ __forceinline__ void interior_cell(int split, int part, int tid, int ntab, int& p, int& a,
+                                                       int& b, int& c, int& s_begin, int& s_end) {
+  int zh;
+  if (split == 2) {
+    const int w = (tid >> 5) & 3, lane = tid & 31;
+    p = 2 * part + (w >> 1);
+    zh = w & 1;
+    const int q = (zh << 5) + lane;
+    a = 2 * (q & 3) + (p & 1);
+    b = 2 * ((q >> 2) & 3) + ((p >> 1) & 1);
+    c = 2 * (q >> 4) + (p >> 2);
+    const int h = (ntab + 1) >> 1;
+    s_begin = tid < 128 ? 0 : h;
+    s_end = tid < 128 ? h : ntab;
+  } else {
+    cell_of(part, tid, p, zh, a, b, c);
+    s_begin = 0;
+    s_end = ntab;
+  }
+}
+
+// C64: the angular-momentum correction of every pair is formed in float64 from the
+// float64 multipoles (mp) and summed in float64, beside the float32 pair without it
+// (a measurement variant of the mixed path; per-kind launches, split 1 only).
+// BLK: stencil entries per float32 partial sum; SPLIT: 1 or 2 (see interior_cell).
+// The kernels are instantiated per shape (a runtime choice inside one kernel made
+// the 80-register variants spill).  Contains a block-wide barrier when SPLIT == 2
+// (every thread reaches it).
+template <bool C64, int BLK, int SPLIT>
+__device__ __forceinline__ void interior_f32(const DevTree& t, int node, int part, const Stencils& st,
                                              const float* __restrict__ mp32, double* __restrict__ loc,
-                                             unsigned char* smem) {
-  int p, zh, a, b, c;
-  cell_of(half, threadIdx.x, p, zh, a, b, c);
+                                             unsigned char* smem, const double* __restrict__ mp) {
   const int lvl = t.level[node];
+  const int ntab = lvl == 0 ? st.n_root : st.n_st;
+  constexpr int split = SPLIT;
+  int p, a, b, c, s_begin, s_end;
+  interior_cell(split, part, threadIdx.x, ntab, p, a, b, c, s_begin, s_end);
   const int64_t NC = t.NC;
   const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
+  double XA64[3], Oh64[10], tOh64[3];
+  DgAcc d64 = {{0.0, 0.0, 0.0}};
+  if constexpr (C64) {
+    for (int i = 0; i < 3; ++i) XA64[i] = mp[(F_X + i) * NC + tgt];
+    const double inv_m = 1.0 / mp[tgt];
+    for (int i = 0; i < 10; ++i) Oh64[i] = mp[(F_O + i) * NC + tgt] * inv_m;
+    tOh64[0] = Oh64[0] + Oh64[3] + Oh64[5];
+    tOh64[1] = Oh64[1] + Oh64[6] + Oh64[8];
+    tOh64[2] = Oh64[2] + Oh64[7] + Oh64[9];
+  }
   float mA, xA[3], QA[6], Oh[10], tOh[3];
   load_mp32(mp32, mp32_base(node, a, b, c), mA, xA, QA, Oh);
   {
@@ -151,14 +197,13 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
     tOh[2] = Oh[2] + Oh[7] + Oh[9];
   }
   const int* tab = lvl == 0 ? st.root : st.parity + p * st.n_st;
-  const int ntab = lvl == 0 ? st.n_root : st.n_st;
   const int* nb = t.nbr + 27 * node;
   float2* sc = reinterpret_cast<float2*>(smem) + threadIdx.x;
   for (int f = 0; f < kInteriorFields; ++f) sc[f * kThreads] = make_float2(0.0f, 0.0f);
-  Acc<float> part;
-  acc_zero(part);
-  for (int s0 = 0; s0 < ntab; s0 += kAccBlock) {
-    const int s1 = min(s0 + kAccBlock, ntab);
+  Acc<float> part_sum;
+  acc_zero(part_sum);
+  for (int s0 = s_begin; s0 < s_end; s0 += BLK) {
+    const int s1 = min(s0 + BLK, s_end);
     for (int s = s0; s < s1; ++s) {
       int dx, dy, dz;
       unpack(__ldg(tab + s), dx, dy, dz);
@@ -172,9 +217,28 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
       const float R1 = xA[1] - (x[1] + 8.0f * (float)oy);
       const float R2 = xA[2] - (x[2] + 8.0f * (float)oz);
       const float rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
-      m2l_pair<true, true>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, part);
+      m2l_pair<true, true, float, Acc<float>, !C64>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, part_sum);
+      if constexpr (C64) {
+        const int64_t src = (int64_t)snode * 512 + (sa & 7) + 8 * (sb & 7) + 64 * (sc & 7);
+        const double S0 = XA64[0] - __ldg(mp + (F_X + 0) * NC + src);
+        const double S1 = XA64[1] - __ldg(mp + (F_X + 1) * NC + src);
+        const double S2 = XA64[2] - __ldg(mp + (F_X + 2) * NC + src);
+        double O64[10];
+        for (int i = 0; i < 10; ++i) O64[i] = __ldg(mp + (F_O + i) * NC + src);
+        corr_pair_f64<true>(S0, S1, S2, __ldg(mp + src), O64, Oh64, tOh64,
+                            rsqrt_f64(fma(S0, S0, fma(S1, S1, S2 * S2))), d64);
+      }
     }
-    flush_partial(part, sc);
+    flush_partial(part_sum, sc);
+  }
+  if constexpr (split == 2) {  // the second stencil half's (sum, compensation) pairs join the first's
+    __syncthreads();
+    if (threadIdx.x >= 128) return;
+    for (int f = 0; f < kInteriorFields; ++f) {
+      const float2 o = sc[f * kThreads + 128];
+      two_sum_into(sc[f * kThreads], o.x);
+      sc[f * kThreads].y += o.y;
+    }
   }
   // sum + compensation in float64; unit cell width -> physical units: L_n scales
   // with h^-(n+1), dg with h^-2
@@ -187,7 +251,11 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int hal
   for (int i = 0; i < 3; ++i) out(G_L1 + i, ih2);
   for (int i = 0; i < 6; ++i) out(G_L2 + i, ih3);
   for (int i = 0; i < 10; ++i) out(G_L3 + i, ih4);
-  for (int i = 0; i < 3; ++i) out(G_DG + i, ih2);
+  if constexpr (C64) {
+    for (int i = 0; i < 3; ++i) loc[(G_DG + i) * NC + tgt] = d64.dg[i];  // physical units already
+  } else {
+    for (int i = 0; i < 3; ++i) out(G_DG + i, ih2);
+  }
 }
 
 // ------------------------------------------------------------ leaf item
@@ -234,16 +302,25 @@ __host__ __device__ inline int halo_index(const HaloGeom& g, int hx, int hy, int
 
 // Shared memory of a leaf item: the far halo (float32 in the mixed path, float64
 // otherwise), and at least 512 x 7 doubles (the boundary results are exchanged
-// through it).  The near item of the mixed path needs the near float64 halo.
-__host__ __device__ inline size_t leaf_smem_bytes(const Stencils& st, bool mixed) {
+// through it).  Mixed path: then, per warp, two staging buffers of one table block
+// (kLeafTableBlockBytes each) and their two mbarriers.  The near item of the mixed
+// path needs the near float64 halo.
+__host__ __device__ inline size_t leaf_halo_bytes(const Stencils& st, bool mixed) {
   const HaloGeom gf = far_geom(st.radius);
   const size_t halo = (mixed ? sizeof(float) : sizeof(double)) * 8 * (size_t)gf.PQ;
-  return halo > sizeof(double) * 512 * 7 ? halo : sizeof(double) * 512 * 7;
+  const size_t b = halo > sizeof(double) * 512 * 7 ? halo : sizeof(double) * 512 * 7;
+  return (b + 127) & ~(size_t)127;
+}
+constexpr int kLeafWarps = kThreads / 32;
+__host__ __device__ inline size_t leaf_smem_bytes(const Stencils& st, bool mixed) {
+  return leaf_halo_bytes(st, mixed) +
+         (mixed ? (size_t)kLeafWarps * (2 * kLeafTableBlockBytes + 2 * sizeof(uint64_t)) : 0);
 }
 
 __host__ __device__ inline size_t near_smem_bytes(const Stencils& st) {
   return sizeof(double) * 8 * (size_t)near_geom(st.near_radius).PQ;
 }
+
 
 // Accumulator of a leaf target (m2l_pair<false, ...> touches only L0, L1, dg).
 template <typename T>
@@ -268,12 +345,12 @@ __device__ __forceinline__ void leaf_merge(A& acc, LeafAcc<float>& p) {
 // M2L from refined same-level neighbours into leaf cell l of a leaf node (leaf
 // target: L0, L1, dg).  The per-cell entry lists hold only offsets whose source
 // lies in the neighbour slot, so every iteration of every lane is a valid pair.
-// Mixed path: plain float32 partial sums of kAccBlock pairs merged into the
+// Mixed path: plain float32 partial sums of st.acc_block pairs merged into the
 // compensated sums of acc (Acc<KF>).
-template <bool MIXED, typename A>
+template <bool MIXED, typename A, bool C64 = false>
 __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l, const Stencils& st,
                                                const double* __restrict__ mp, const float* __restrict__ mp32,
-                                               A& acc) {
+                                               A& acc, DgAcc* d64 = nullptr) {
   using T = typename std::conditional<MIXED, float, double>::type;
   const int64_t NC = t.NC;
   const int a = l & 7, b = (l >> 3) & 7, c = l >> 6;
@@ -328,8 +405,17 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
         rinv = rsqrt_f64(fma(R0, R0, fma(R1, R1, R2 * R2)));
       }
       if constexpr (MIXED) {
-        m2l_pair<false, false>(R0, R1, R2, m, Q, O, zero10, zero10, rinv, part);
-        if (++n_part == kAccBlock) {
+        m2l_pair<false, false, float, LeafAcc<float>, !C64>(R0, R1, R2, m, Q, O, zero10, zero10, rinv, part);
+        if constexpr (C64) {
+          const double S0 = mp[(F_X + 0) * NC + tgt] - __ldg(mp + (F_X + 0) * NC + src);
+          const double S1 = mp[(F_X + 1) * NC + tgt] - __ldg(mp + (F_X + 1) * NC + src);
+          const double S2 = mp[(F_X + 2) * NC + tgt] - __ldg(mp + (F_X + 2) * NC + src);
+          double O64[10];
+          for (int i = 0; i < 10; ++i) O64[i] = __ldg(mp + (F_O + i) * NC + src);
+          corr_pair_f64<false>(S0, S1, S2, __ldg(mp + src), O64, nullptr, nullptr,
+                               rsqrt_f64(fma(S0, S0, fma(S1, S1, S2 * S2))), *d64);
+        }
+        if (++n_part == st.acc_block) {
           leaf_merge(acc, part);
           n_part = 0;
         }
@@ -410,7 +496,7 @@ __host__ __device__ __forceinline__ int leaf_cell(int q, int tid) {
 // computes its cell of each half.  Mixed path: the float32 far field only (the
 // float64 near field is the separate near item, so that the two can run side by
 // side on an SM); float64 path: far and near field.
-template <bool MIXED>
+template <bool MIXED, bool C64 = false>
 __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Stencils& st,
                                           const double* __restrict__ mp, const float* __restrict__ mp32,
                                           double* __restrict__ loc, unsigned char* smem) {
@@ -430,11 +516,22 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
   double L0[2], L1[2][3];  // the thread's two cells (see leaf_cell)
   if (MIXED) {
     // warp w = parity class w; lane (i, j, k0) owns the cells with c / 2 = k0 and
-    // k0 + 2: both share every stencil entry (one table and one kernel load feed
-    // two halo reads and eight fused multiply-adds)
-    const int lane = threadIdx.x & 31;
-    const int2* __restrict__ far = (lvl == 0 ? st.leaf_root : st.leaf_far) + (threadIdx.x >> 5) * n_far;
-    const float4* __restrict__ fk = st.leaf_k32 + (lvl == 0 ? 8 * st.n_st : 0) + (threadIdx.x >> 5) * n_far;
+    // k0 + 2: both share every stencil entry (one table entry feeds two halo reads
+    // and eight fused multiply-adds).  The warp's stencil table streams through
+    // shared memory in blocks of kLeafBlock entries (halo offsets, then float32
+    // kernel rows; kLeafTableBlockBytes per block), each fetched by one bulk
+    // asynchronous copy (TMA) issued a block ahead into the other of two buffers,
+    // so the entries are read from shared memory instead of L2.
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nblk = (n_far + kLeafBlock - 1) / kLeafBlock;
+    const unsigned char* gtab = reinterpret_cast<const unsigned char*>(st.leaf_blocks) +
+                                ((lvl == 0 ? (size_t)8 * st.far_blocks + (size_t)w * st.root_blocks
+                                           : (size_t)w * st.far_blocks) *
+                                 kLeafTableBlockBytes);
+    unsigned char* sbuf = smem + leaf_halo_bytes(st, true) + (size_t)w * 2 * kLeafTableBlockBytes;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + leaf_halo_bytes(st, true) +
+                                                (size_t)kLeafWarps * 2 * kLeafTableBlockBytes) +
+                    2 * w;
     const int lane_f = (lane & 3) + gf.PY * ((lane >> 2) & 3) + gf.PZ * (lane >> 4);
     const int dz = 2 * gf.PZ;
     KF f[2][4];
@@ -442,36 +539,61 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
     for (int q = 0; q < 2; ++q)
 #pragma unroll
       for (int k = 0; k < 4; ++k) f[q][k] = 0.0f;
-    // one stencil entry: the two cells' masses times the entry's kernel row
-    auto entry = [&](int s, float* pa, float* pb) {
-      const int off = __ldg(&far[s].x);
-      const float4 k = __ldg(fk + s);
-      const float m0 = halo32[lane_f + off], m1 = halo32[lane_f + off + dz];
-      pa[0] = fmaf(m0, k.x, pa[0]);
-      pa[1] = fmaf(m0, k.y, pa[1]);
-      pa[2] = fmaf(m0, k.z, pa[2]);
-      pa[3] = fmaf(m0, k.w, pa[3]);
-      pb[0] = fmaf(m1, k.x, pb[0]);
-      pb[1] = fmaf(m1, k.y, pb[1]);
-      pb[2] = fmaf(m1, k.z, pb[2]);
-      pb[3] = fmaf(m1, k.w, pb[3]);
-    };
-    // full blocks of kAccBlock entries fully unrolled (constant offsets into the
-    // tables, no per-entry loop control), then the last partial block
-    int s0i = 0;
-    for (; s0i + kAccBlock <= n_far; s0i += kAccBlock) {
-      float pa[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-      for (int u = 0; u < kAccBlock; ++u) entry(s0i + u, pa, pb);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) f[0][k].add(pa[k]), f[1][k].add(pb[k]);
+    if (lane == 0) {
+      tma::mbar_init(bar);
+      tma::mbar_init(bar + 1);
+      tma::fence_mbar_init();
+      tma::fence_proxy_async();  // earlier items wrote this shared memory
+      tma::mbar_expect_tx(bar, kLeafTableBlockBytes);
+      tma::copy_g2s(sbuf, gtab, kLeafTableBlockBytes, bar);
     }
-    if (s0i < n_far) {
+    __syncwarp();
+    bool ok = true;
+    int b = 0;
+    for (; b < nblk; ++b) {
+      if (lane == 0 && b + 1 < nblk) {  // the next block into the other buffer
+        unsigned char* nb = sbuf + ((b + 1) & 1) * kLeafTableBlockBytes;
+        tma::fence_proxy_async();
+        tma::mbar_expect_tx(bar + ((b + 1) & 1), kLeafTableBlockBytes);
+        tma::copy_g2s(nb, gtab + (size_t)(b + 1) * kLeafTableBlockBytes, kLeafTableBlockBytes, bar + ((b + 1) & 1));
+      }
+      ok = __all_sync(0xffffffffu, tma::mbar_wait(bar + (b & 1), (b >> 1) & 1));
+      if (!ok) break;
+      const int* offs = reinterpret_cast<const int*>(sbuf + (b & 1) * kLeafTableBlockBytes);
+      const float4* ks = reinterpret_cast<const float4*>(offs + kLeafBlock);
+      // one stencil entry: the two cells' masses times the entry's kernel row
+      auto entry = [&](int u, float* pa, float* pb) {
+        const int off = offs[u];
+        const float4 k = ks[u];
+        const float m0 = halo32[lane_f + off], m1 = halo32[lane_f + off + dz];
+        pa[0] = fmaf(m0, k.x, pa[0]);
+        pa[1] = fmaf(m0, k.y, pa[1]);
+        pa[2] = fmaf(m0, k.z, pa[2]);
+        pa[3] = fmaf(m0, k.w, pa[3]);
+        pb[0] = fmaf(m1, k.x, pb[0]);
+        pb[1] = fmaf(m1, k.y, pb[1]);
+        pb[2] = fmaf(m1, k.z, pb[2]);
+        pb[3] = fmaf(m1, k.w, pb[3]);
+      };
       float pa[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      const int n_in = min(kLeafBlock, n_far - b * kLeafBlock);
+      if (n_in == kLeafBlock) {  // full block fully unrolled (constant offsets, no loop control)
+#pragma unroll
+        for (int u = 0; u < kLeafBlock; ++u) entry(u, pa, pb);
+      } else {
 #pragma unroll 4
-      for (int s = s0i; s < n_far; ++s) entry(s, pa, pb);
+        for (int u = 0; u < n_in; ++u) entry(u, pa, pb);
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) f[0][k].add(pa[k]), f[1][k].add(pb[k]);
+      __syncwarp();  // every lane has read this buffer before it is refilled
+    }
+    if (!ok) {
+      // a copy did not complete in time: report it, let the copies in flight land
+      // (bounded), and leave this item's far field incomplete
+      if (lane == 0) atomicOr(st.err, kErrTimeout);
+      tma::mbar_wait(bar + (b & 1), (b >> 1) & 1);
+      if (b + 1 < nblk) tma::mbar_wait(bar + ((b + 1) & 1), ((b + 1) >> 1) & 1);
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -537,9 +659,11 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
       if constexpr (MIXED) {
         Acc<KF> acc;
         acc_zero(acc);
-        boundary_pairs<true>(t, node, lb, st, mp, mp32, acc);
+        DgAcc d64 = {{0.0, 0.0, 0.0}};
+        boundary_pairs<true, Acc<KF>, C64>(t, node, lb, st, mp, mp32, acc, &d64);
         v[0] = acc.L0.value() * ih;
-        for (int i = 0; i < 3; ++i) v[1 + i] = acc.L1[i].value() * ih2, v[4 + i] = acc.dg[i].value() * ih2;
+        for (int i = 0; i < 3; ++i)
+          v[1 + i] = acc.L1[i].value() * ih2, v[4 + i] = C64 ? d64.dg[i] : acc.dg[i].value() * ih2;
       } else {
         Acc<double> acc;
         acc_zero(acc);

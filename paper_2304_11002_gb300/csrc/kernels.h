@@ -14,6 +14,13 @@ struct alignas(16) Kappa {
   double v[4];
 };
 
+// Stencil entries per float32 partial sum of the leaf far field (a fully unrolled
+// block), and the bytes of one block of the mixed path's leaf table: kLeafBlock
+// int32 halo offsets, then kLeafBlock float4 kernel rows (a multiple of 16 bytes,
+// one bulk asynchronous copy).
+constexpr int kLeafBlock = 32;
+constexpr int kLeafTableBlockBytes = kLeafBlock * (4 + 16);
+
 struct Stencils {
   const int* parity;  // [8][n_st] packed offsets
   int n_st;
@@ -22,9 +29,11 @@ struct Stencils {
   const int* near_;   // non-zero near offsets
   int n_near;
   const Kappa* kappa;    // dense monopole kernel table over [-R, R]^3, unit cell width
-  const float4* leaf_k32; // mixed path: the float32 kernel row of every leaf_far entry
-                          // ([8][n_st]), then of every leaf_root entry ([8][n_root]),
-                          // inline in table order (no dependent row lookup)
+  const uint4* leaf_blocks;  // mixed path: the leaf far-field tables in blocks of 32 entries
+                             // (32 int32 halo offsets, then 32 float4 kernel rows, 640
+                             // bytes; zero-padded): [8][far_blocks] for the parity
+                             // stencils, then [8][root_blocks] for the level-0 stencil
+  int far_blocks, root_blocks;
   int radius;            // R: maximum |offset component|
   int near_radius;       // maximum |offset component| of the near offsets
   const int* cell_ent;   // parity offsets per (cell, neighbour slot), see Plan::cell_ent
@@ -36,6 +45,12 @@ struct Stencils {
   const int2* leaf_far;   // [8][n_st]   parity stencil (far halo)
   const int2* leaf_root;  // [8][n_root] level-0 stencil (far halo)
   const int2* leaf_near;  // [8][n_near] near offsets (mixed: near float64 halo; float64: far halo)
+  // Shape of the mixed-precision interior items, chosen by the autotuner:
+  int* err = nullptr;       // device error word of the handle (kErrTimeout: a bounded wait ran out)
+  int acc_block = 32;       // stencil entries per float32 partial sum before the compensated merge (32, 64)
+  int interior_split = 1;   // 1: an item is half a node, one thread per target cell;
+                            // 2: an item is a quarter node, two threads per target cell (one
+                            //    stencil half each, merged at the end)
 };
 
 // Host: the leaf-item tables above for the given stencils and precision mode.
@@ -68,8 +83,9 @@ constexpr int kCrossSlicesPerItem = 64;
 // mp32 (may be null): float32 copy of the multipoles for the mixed-precision path.
 cudaError_t launch_init_leaf(const DevTree& t, const int* leaf_nodes, int n_leaf_nodes, double* mp, float* mp32,
                              cudaStream_t s);
+// err: device word; kErrDensity is set when a density is not finite and positive.
 cudaError_t launch_p2m(const DevTree& t, const int* leaf_nodes, int n_leaf_nodes, const double* rho, double* mp,
-                       float* mp32, cudaStream_t s);
+                       float* mp32, int* err, cudaStream_t s);
 cudaError_t launch_m2m(const DevTree& t, int node_begin, int node_end, double* mp, float* mp32, cudaStream_t s);
 // nearf (may be null): [4][n_leaf_cells] near-field L0, L1 of the leaf cells, added at L2P.
 cudaError_t launch_l2l(const DevTree& t, int node_begin, int node_end, const double* mp, double* loc, double* phi,
@@ -88,13 +104,15 @@ struct InteractArgs {
   int n_leaf;
   double* nearf;       // mixed precision: [4][NL] near-field sums of the leaf cells (near items)
   int64_t NL;          // leaf cells
-  const int* queue;    // persistent queue: (node << 3) | (kind << 1) | half, see kernels_interact.cu
+  const int* queue;    // persistent queue: (node << 4) | (kind << 2) | part, see kernels_interact.cu
   int n_items;
   int* counter;        // work counter of the persistent launch (device scratch)
   int grid;            // blocks of the persistent launch (SMs x resident blocks per SM)
   int min_blocks;      // launch-bounds variant of the persistent kernel (1, 2 or 3)
   CrossCells xc;       // tabulated cross-level pairs: cross items of the persistent queue
   double* xcf;         // [4][32 * xc.n_slices] their per-slot sums (persistent mode)
+  bool corr64 = false; // mixed precision: the angular-momentum correction in float64
+                       // (measurement variant; per-kind launches only)
 };
 // Once per process and device (opts the leaf-item kernels into large shared memory).
 cudaError_t configure_interact_kernels();
@@ -108,8 +126,9 @@ cudaError_t launch_near_items(const DevTree& t, const InteractArgs& a, cudaStrea
 cudaError_t launch_persistent(const DevTree& t, const InteractArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------ cross-level pairs (kernels_boundary.cu)
+// corr64 (mixed only): the angular-momentum correction of the far pairs in float64.
 cudaError_t launch_cross_list(const DevTree& t, const CrossList& xl, bool full, const double* mp, double* loc,
-                              bool mixed, cudaStream_t s);
+                              bool mixed, cudaStream_t s, bool corr64 = false);
 // Tabulated point-mass pairs, float64 in both precision modes.  grid: a multiple of
 // the SM count (cross_cells_blocks_per_sm gives the resident blocks per SM).
 cudaError_t cross_cells_blocks_per_sm(const CrossCells& xc, int* blocks);

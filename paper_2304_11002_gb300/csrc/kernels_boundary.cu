@@ -108,7 +108,9 @@ __global__ void __launch_bounds__(kCrossCellsThreads) k_cross_cells_adjoint(DevT
   }
 }
 
-template <bool FULL, bool MIXED>
+// C64 (mixed only): the correction of the far pairs in float64 from the float64
+// multipoles, summed in float64 (measurement variant).
+template <bool FULL, bool MIXED, bool C64 = false>
 __global__ void __launch_bounds__(128) k_cross_w(DevTree t, CrossList xl, const double* __restrict__ mp,
                                                  double* __restrict__ loc) {
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(128) k_cross_w(DevTree t, CrossList xl, const 
     for (int k = 0; k < 3; ++k) tOh32[k] = FULL ? (float)(tOh[k] * ih3) : 0.0f;
     Acc<KF> acc;
     acc_zero(acc);
+    DgAcc d64 = {{0.0, 0.0, 0.0}};
     for (int64_t e = e0 + lane; e < em; e += 32) {
       const int64_t src = xl.sources[e];
       const float R0 = (float)((XA0 - mp[(F_X + 0) * NC + src]) * ih);
@@ -145,13 +148,20 @@ __global__ void __launch_bounds__(128) k_cross_w(DevTree t, CrossList xl, const 
       for (int k = 0; k < 6; ++k) Q[k] = (float)(mp[(F_Q + k) * NC + src] * ih2);
       for (int k = 0; k < 10; ++k) O[k] = (float)(mp[(F_O + k) * NC + src] * ih3);
       const float rinv = rsqrt_f32(fmaf(R0, R0, fmaf(R1, R1, R2 * R2)));
-      m2l_pair<FULL, FULL>(R0, R1, R2, (float)mp[src], Q, O, Oh32, tOh32, rinv, acc);
+      m2l_pair<FULL, FULL, float, Acc<KF>, !C64>(R0, R1, R2, (float)mp[src], Q, O, Oh32, tOh32, rinv, acc);
+      if constexpr (C64) {
+        const double S0 = XA0 - mp[(F_X + 0) * NC + src], S1 = XA1 - mp[(F_X + 1) * NC + src],
+                     S2 = XA2 - mp[(F_X + 2) * NC + src];
+        double O64[10];
+        for (int k = 0; k < 10; ++k) O64[k] = mp[(F_O + k) * NC + src];
+        corr_pair_f64<FULL>(S0, S1, S2, mp[src], O64, Oh, tOh, rsqrt_f64(fma(S0, S0, fma(S1, S1, S2 * S2))), d64);
+      }
     }
     const double ih4 = ih2 * ih2;
     d.L0 = acc.L0.value() * ih;
     for (int k = 0; k < 3; ++k) {
       d.L1[k] = acc.L1[k].value() * ih2;
-      d.dg[k] = acc.dg[k].value() * ih2;
+      d.dg[k] = C64 ? d64.dg[k] : acc.dg[k].value() * ih2;
       d.V[k] = acc.V[k].value() * ih4;
     }
     for (int k = 0; k < 6; ++k) d.L2[k] = acc.L2[k].value() * ih3;
@@ -242,10 +252,15 @@ cudaError_t launch_cross_cells_adjoint(const DevTree& t, const CrossCells& xc, c
 }
 
 cudaError_t launch_cross_list(const DevTree& t, const CrossList& xl, bool full, const double* mp, double* loc,
-                              bool mixed, cudaStream_t s) {
+                              bool mixed, cudaStream_t s, bool corr64) {
   if (xl.n_targets == 0) return cudaSuccess;
   const int blocks = (int)(((int64_t)xl.n_targets * 32 + 127) / 128);
-  if (full) {
+  if (mixed && corr64) {
+    if (full)
+      k_cross_w<true, true, true><<<blocks, 128, 0, s>>>(t, xl, mp, loc);
+    else
+      k_cross_w<false, true, true><<<blocks, 128, 0, s>>>(t, xl, mp, loc);
+  } else if (full) {
     if (mixed)
       k_cross_w<true, true><<<blocks, 128, 0, s>>>(t, xl, mp, loc);
     else

@@ -31,15 +31,22 @@ __global__ void k_init_leaf(DevTree t, const int* __restrict__ nodes, double* __
 }
 
 // P2M: a leaf cell is one monopole m = rho h^3 at its centre (Section IV-C).
+// The density must be finite and positive (centres of mass divide by the mass):
+// any other value sets kErrDensity in *err, read back by octo_fmm_stats and
+// octo_fmm_forces_host.  The check changes no result.  Blocks of 256 threads run
+// two full passes over the 512 cells, so every warp votes with all lanes.
 __global__ void k_p2m(DevTree t, const int* __restrict__ nodes, const double* __restrict__ rho,
-                      double* __restrict__ mp, float* __restrict__ mp32) {
+                      double* __restrict__ mp, float* __restrict__ mp32, int* __restrict__ err) {
   const int node = nodes[blockIdx.x];
   const double h3 = t.h3[t.level[node]];
   const int64_t lid = t.leaf_id[node];
   for (int l = threadIdx.x; l < 512; l += blockDim.x) {
-    const double m = rho[lid * 512 + l] * h3;
+    const double r = rho[lid * 512 + l];
+    const double m = r * h3;
     mp[(int64_t)node * 512 + l] = m;
     if (mp32) mp32[4 * mp32_base(node, l & 7, (l >> 3) & 7, l >> 6)] = (float)m;
+    const bool bad = !(r > 0.0 && isfinite(r));  // NaN, <= 0 or +inf
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrDensity);
   }
 }
 
@@ -61,7 +68,7 @@ __global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_beg
   const int o = (a >> 2) + 2 * (b >> 2) + 4 * (c >> 2);
   const int ch = t.children[8 * node + o];
   // a leaf child node's cells are point masses (P2M): their moments are zero, so
-  // they are not read (the same expressions then run on zeros)
+  // they are neither read nor added
   const bool leaf_child = t.children[8 * ch] < 0;
   const int64_t NC = t.NC;
   // child cell e = ex + 2 ey + 4 ez of this parent cell
@@ -81,6 +88,36 @@ __global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_beg
   X1 /= m;
   X2 /= m;
   double Q[6] = {0, 0, 0, 0, 0, 0}, O[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (leaf_child) {
+    // point-mass children: M2 = sum m d d, M3 = sum m d d d (the general expressions
+    // below with zero child moments and their zero terms left out; fused
+    // multiply-adds may round differently)
+#pragma unroll 1
+    for (int e = 0; e < 8; ++e) {
+      const int64_t ce = child(e);
+      const double mc = mp[ce];
+      const double d0 = mp[(F_X + 0) * NC + ce] - X0;
+      const double d1 = mp[(F_X + 1) * NC + ce] - X1;
+      const double d2 = mp[(F_X + 2) * NC + ce] - X2;
+      const double md0 = mc * d0, md1 = mc * d1, md2 = mc * d2;
+      Q[0] += md0 * d0;
+      Q[1] += md0 * d1;
+      Q[2] += md0 * d2;
+      Q[3] += md1 * d1;
+      Q[4] += md1 * d2;
+      Q[5] += md2 * d2;
+      O[0] += md0 * d0 * d0;
+      O[1] += md0 * d0 * d1;
+      O[2] += md0 * d0 * d2;
+      O[3] += md0 * d1 * d1;
+      O[4] += md0 * d1 * d2;
+      O[5] += md0 * d2 * d2;
+      O[6] += md1 * d1 * d1;
+      O[7] += md1 * d1 * d2;
+      O[8] += md1 * d2 * d2;
+      O[9] += md2 * d2 * d2;
+    }
+  } else {
 #pragma unroll 1
   for (int e = 0; e < 8; ++e) {
     const int64_t ce = child(e);
@@ -89,9 +126,9 @@ __global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_beg
     const double d1 = mp[(F_X + 1) * NC + ce] - X1;
     const double d2 = mp[(F_X + 2) * NC + ce] - X2;
     double q[6];
-    for (int i = 0; i < 6; ++i) q[i] = leaf_child ? 0.0 : mp[(F_Q + i) * NC + ce];
+    for (int i = 0; i < 6; ++i) q[i] = mp[(F_Q + i) * NC + ce];
     double oc[10];
-    for (int i = 0; i < 10; ++i) oc[i] = leaf_child ? 0.0 : mp[(F_O + i) * NC + ce];
+    for (int i = 0; i < 10; ++i) oc[i] = mp[(F_O + i) * NC + ce];
     const double md0 = mc * d0, md1 = mc * d1, md2 = mc * d2;
     Q[0] += q[0] + md0 * d0;
     Q[1] += q[1] + md0 * d1;
@@ -110,6 +147,7 @@ __global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_beg
     O[7] += oc[7] + q[3] * d2 + 2.0 * q[4] * d1 + md1 * d1 * d2;        // yyz
     O[8] += oc[8] + 2.0 * q[4] * d2 + q[5] * d1 + md1 * d2 * d2;        // yzz
     O[9] += oc[9] + 3.0 * q[5] * d2 + md2 * d2 * d2;                    // zzz
+  }
   }
   const int64_t pc = (int64_t)node * 512 + l;
   mp[pc] = m;
@@ -232,9 +270,9 @@ cudaError_t launch_init_leaf(const DevTree& t, const int* leaf_nodes, int n, dou
 }
 
 cudaError_t launch_p2m(const DevTree& t, const int* leaf_nodes, int n, const double* rho, double* mp, float* mp32,
-                       cudaStream_t s) {
+                       int* err, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_p2m<<<n, 256, 0, s>>>(t, leaf_nodes, rho, mp, mp32);
+  k_p2m<<<n, 256, 0, s>>>(t, leaf_nodes, rho, mp, mp32, err);
   return cudaGetLastError();
 }
 

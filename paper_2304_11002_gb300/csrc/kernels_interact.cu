@@ -9,35 +9,18 @@
 //    others.  The counter is reset by a memset issued before every launch; no block
 //    ever waits for another.
 // The autotuner in capi.cu times both on the actual tree and keeps the faster.
-#include <algorithm>
-
-#include "cross.cuh"
-#include "items.cuh"
+#include "interact.cuh"
 
 namespace octo {
 
 namespace {
 
-template <bool MIXED>
-__global__ void __launch_bounds__(items::kThreads, MIXED ? 3 : 1) k_interior_items(DevTree t, const int* __restrict__ nodes,
-                                                                     Stencils st, const double* __restrict__ mp,
-                                                                     const float* __restrict__ mp32,
-                                                                     double* __restrict__ loc) {
+template <bool MIXED, bool C64 = false>
+__global__ void __launch_bounds__(items::kThreads, MIXED && !C64 ? 3 : 1)
+    k_leaf_items(DevTree t, const int* __restrict__ nodes, Stencils st, const double* __restrict__ mp,
+                 const float* __restrict__ mp32, double* __restrict__ loc) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int node = nodes[blockIdx.x >> 1];
-  if (MIXED)
-    items::interior_f32(t, node, blockIdx.x & 1, st, mp32, loc, smem);
-  else
-    items::interior_f64(t, node, blockIdx.x & 1, st, mp, loc);
-}
-
-template <bool MIXED>
-__global__ void __launch_bounds__(items::kThreads, MIXED ? 3 : 1) k_leaf_items(DevTree t, const int* __restrict__ nodes, Stencils st,
-                                                                 const double* __restrict__ mp,
-                                                                 const float* __restrict__ mp32,
-                                                                 double* __restrict__ loc) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  items::leaf_item<MIXED>(t, nodes[blockIdx.x], st, mp, mp32, loc, smem);
+  items::leaf_item<MIXED, C64>(t, nodes[blockIdx.x], st, mp, mp32, loc, smem);
 }
 
 __global__ void __launch_bounds__(items::kThreads) k_near_items(DevTree t, const int* __restrict__ nodes, Stencils st,
@@ -45,82 +28,6 @@ __global__ void __launch_bounds__(items::kThreads) k_near_items(DevTree t, const
                                                                  double* __restrict__ nearf, int64_t NL) {
   extern __shared__ __align__(16) unsigned char smem[];
   items::near_item(t, nodes[blockIdx.x], st, mp, nearf, NL, smem);
-}
-
-// item = (node << 3) | (kind << 1) | half; kind 0 = interior (one half of the node),
-// 1 = leaf (the whole node), 2 = near field of a leaf node (mixed precision only),
-// 3 = kCrossSlicesPerItem slices of the tabulated cross-level pairs starting at
-// slice node * kCrossSlicesPerItem (sums per slot into xcf; k_cross_apply adds them
-// to the targets after the launch, so that no item writes what another one reads)
-template <bool MIXED, int MINB>
-__global__ void __launch_bounds__(items::kThreads, MINB)
-    k_persistent(DevTree t, const int* __restrict__ queue, int n_items, int* __restrict__ counter, Stencils st,
-                 const double* __restrict__ mp, const float* __restrict__ mp32, double* __restrict__ loc,
-                 double* __restrict__ nearf, int64_t NL, CrossCells xc, double* __restrict__ xcf) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int next;
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
-    __syncthreads();
-    const int k = next;
-    if (k >= n_items) return;
-    const int it = queue[k];
-    const int node = it >> 3, half = it & 1, kind = (it >> 1) & 3;
-    if (kind == 3) {
-      double2* tab2 = reinterpret_cast<double2*>(smem);
-      cross::stage_table(xc, tab2);
-      __syncthreads();
-      const int lane = threadIdx.x & 31;
-      const int s1 = min((node + 1) * kCrossSlicesPerItem, xc.n_slices);
-      const int64_t n_slots = (int64_t)xc.n_slices * 32;
-      for (int sl = node * kCrossSlicesPerItem + (threadIdx.x >> 5); sl < s1; sl += items::kThreads / 32) {
-        double S[4];
-        cross::slice_sums(xc, tab2, mp, sl, lane, S);
-        const int64_t slot = (int64_t)sl * 32 + lane;
-        for (int k = 0; k < 4; ++k) xcf[k * n_slots + slot] = S[k];
-      }
-    } else if (kind == 2) {
-      if (MIXED) items::near_item(t, node, st, mp, nearf, NL, smem);
-    } else if (kind == 1) {
-      items::leaf_item<MIXED>(t, node, st, mp, mp32, loc, smem);
-    } else {
-      if (MIXED)
-        items::interior_f32(t, node, half, st, mp32, loc, smem);
-      else
-        items::interior_f64(t, node, half, st, mp, loc);
-    }
-  }
-}
-
-// Dynamic shared memory of the persistent kernel: the largest of its item kinds
-// (float64 interior items use none; cross items hold the cross kernel table).
-size_t persistent_smem_bytes(const Stencils& st, const CrossCells& xc, bool mixed) {
-  const size_t leaf = items::leaf_smem_bytes(st, mixed), cross = sizeof(double) * 4 * (size_t)xc.n_rows;
-  return std::max(cross, mixed ? std::max({leaf, items::near_smem_bytes(st), items::interior_smem_bytes()}) : leaf);
-}
-
-// Resident blocks per SM of a persistent variant (sets its shared-memory limit);
-// called once per handle, outside any stream capture.
-template <bool MIXED, int MINB>
-cudaError_t persistent_occupancy(const Stencils& st, const CrossCells& xc, int* per_sm) {
-  const size_t smem = persistent_smem_bytes(st, xc, MIXED);
-  cudaError_t e = cudaFuncSetAttribute(k_persistent<MIXED, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_persistent<MIXED, MINB>, items::kThreads, smem);
-  if (e == cudaSuccess && *per_sm < 1) e = cudaErrorInvalidConfiguration;
-  return e;
-}
-
-template <bool MIXED, int MINB>
-cudaError_t persistent_launch(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
-  const size_t smem = persistent_smem_bytes(a.st, a.xc, MIXED);
-  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  k_persistent<MIXED, MINB><<<a.grid, items::kThreads, smem, s>>>(t, a.queue, a.n_items, a.counter, a.st, a.mp,
-                                                                  a.mp32, a.loc, a.nearf, a.NL, a.xc, a.xcf);
-  return cudaGetLastError();
 }
 
 }  // namespace
@@ -147,23 +54,30 @@ cudaError_t configure_interact_kernels() {
   const int big = 200 * 1024;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leaf_items<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_leaf_items<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_leaf_items<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   return e;
 }
 
 cudaError_t launch_interior_items(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
   if (a.n_interior == 0) return cudaSuccess;
-  if (a.mixed)
-    k_interior_items<true><<<2 * a.n_interior, items::kThreads, items::interior_smem_bytes(), s>>>(
+  if (a.mixed && a.corr64) {
+    k_interior_items<true, true, 32, 1><<<2 * a.n_interior, items::kThreads, items::interior_smem_bytes(), s>>>(
         t, a.interior, a.st, a.mp, a.mp32, a.loc);
-  else
-    k_interior_items<false><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp, a.mp32, a.loc);
+    return cudaGetLastError();
+  }
+  if (a.mixed) return a.st.acc_block == 64 ? interior_items_b64(t, a, s) : MixedShapes<32>::interior(t, a, s);
+  k_interior_items<false, false, 32, 1><<<2 * a.n_interior, items::kThreads, 0, s>>>(t, a.interior, a.st, a.mp,
+                                                                                     a.mp32, a.loc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_leaf_items(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
   if (a.n_leaf == 0) return cudaSuccess;
   const size_t smem = items::leaf_smem_bytes(a.st, a.mixed);
-  if (a.mixed)
+  if (a.mixed && a.corr64)
+    k_leaf_items<true, true><<<a.n_leaf, items::kThreads, smem, s>>>(t, a.leaf, a.st, a.mp, a.mp32, a.loc);
+  else if (a.mixed)
     k_leaf_items<true><<<a.n_leaf, items::kThreads, smem, s>>>(t, a.leaf, a.st, a.mp, a.mp32, a.loc);
   else
     k_leaf_items<false><<<a.n_leaf, items::kThreads, smem, s>>>(t, a.leaf, a.st, a.mp, a.mp32, a.loc);
@@ -177,27 +91,30 @@ cudaError_t launch_near_items(const DevTree& t, const InteractArgs& a, cudaStrea
 }
 
 // Register budgets: 1 or 2 resident blocks per SM, and 3 in mixed precision (whose
-// items all fit 85 registers; the float64 interior item needs twice that).
+// items all fit 85 registers; the float64 interior item needs twice that).  Mixed
+// precision: the fewest resident blocks over every interior shape of the budget
+// (sets every variant's shared-memory limit).
 cudaError_t persistent_blocks_per_sm(bool mixed, int min_blocks, const Stencils& st, const CrossCells& xc,
                                      int* per_sm) {
   if (mixed) {
-    if (min_blocks == 3) return persistent_occupancy<true, 3>(st, xc, per_sm);
-    return min_blocks == 2 ? persistent_occupancy<true, 2>(st, xc, per_sm)
-                           : persistent_occupancy<true, 1>(st, xc, per_sm);
+    if (min_blocks < 1 || min_blocks > 3) return cudaErrorInvalidValue;
+    int a = 0, b = 0;
+    cudaError_t e = MixedShapes<32>::occupancy(min_blocks, st, xc, &a);
+    if (e == cudaSuccess) e = persistent_occupancy_b64(min_blocks, st, xc, &b);
+    *per_sm = std::min(a, b);
+    return e;
   }
   if (min_blocks == 3) return cudaErrorInvalidValue;
-  return min_blocks == 2 ? persistent_occupancy<false, 2>(st, xc, per_sm) : persistent_occupancy<false, 1>(st, xc, per_sm);
+  return min_blocks == 2 ? persistent_occupancy<false, 2, 32, 1>(st, xc, per_sm)
+                         : persistent_occupancy<false, 1, 32, 1>(st, xc, per_sm);
 }
 
 cudaError_t launch_persistent(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
   if (a.n_items == 0) return cudaSuccess;
-  if (a.grid < 1) return cudaErrorInvalidConfiguration;
-  if (a.mixed) {
-    if (a.min_blocks == 3) return persistent_launch<true, 3>(t, a, s);
-    return a.min_blocks == 2 ? persistent_launch<true, 2>(t, a, s) : persistent_launch<true, 1>(t, a, s);
-  }
+  if (a.grid < 1 || a.corr64) return cudaErrorInvalidConfiguration;  // float64 correction: per-kind launches only
+  if (a.mixed) return a.st.acc_block == 64 ? persistent_b64(t, a, s) : MixedShapes<32>::persistent(t, a, s);
   if (a.min_blocks == 3) return cudaErrorInvalidValue;
-  return a.min_blocks == 2 ? persistent_launch<false, 2>(t, a, s) : persistent_launch<false, 1>(t, a, s);
+  return a.min_blocks == 2 ? persistent_launch<false, 2, 32, 1>(t, a, s) : persistent_launch<false, 1, 32, 1>(t, a, s);
 }
 
 }  // namespace octo

@@ -10,6 +10,11 @@
 // interaction step, the workspace that octo_fmm_forces keeps in handle-owned memory -
 // lives in one fixed file-scope device array.
 //
+// With CUDA's lazy module loading (the default), the first use of this file's kernels
+// or of the array on a device - the first call on that device - loads the module,
+// and that load is when the driver reserves the array and the module's code.  Every
+// later call allocates nothing.
+//
 // For a tree of one leaf node every pair of distinct cells is either well separated
 // (M2L between two monopoles at cell centres) or near (P2P); both are the exact
 // point-mass interaction, so each subgrid's result is its direct sum.
@@ -113,6 +118,10 @@ extern "C" int octo_fmm_subgrids_noalloc(int n_subgrids, const double* rho_dev, 
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int n = n_subgrids;
+  // A launch error is read with cudaGetLastError, which also returns (and clears) an
+  // error left by an earlier, unrelated runtime call of this thread: take that one
+  // first, so that it is not reported as a failure of these launches.
+  (void)cudaGetLastError();
   k_noalloc_p2m<<<(n * 512 + 255) / 256, 256, 0, s>>>(rho_dev, h * h * h, n, mass);
   k_noalloc_cells<<<n, 512, 0, s>>>(mass, h, n, phi_dev, g_dev);
   e = cudaGetLastError();

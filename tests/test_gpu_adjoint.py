@@ -53,10 +53,26 @@ def test_adjoint_matches_oracle_vjp(which):
     assert err <= 1e-11, err
 
 
-def test_adjoint_dot_product_adaptive():
-    """<v, J u> (oracle complex step, sampled) against <J^T v, u> (GPU adjoint) on a
-    4-level adaptive binary with cross-level pairs."""
+def test_adjoint_matches_oracle_vjp_adaptive4():
+    """Element by element on the 4-level adaptive binary (interior nodes on three
+    levels, refinement boundaries, tabulated and general cross-level pairs)."""
     w = W.adaptive_binary(3, 0.08)
+    tree, rho = w.tree, w.rho.reshape(-1)
+    n = rho.size
+    rng = np.random.default_rng(34)
+    vphi, vg = rng.normal(size=n), rng.normal(size=(3, n))
+    got = _gpu_vjp(tree, rho, vphi, vg)
+    ref = oracle.fmm_vjp(tree, rho, vphi, vg)
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err <= 1e-11, err
+
+
+@pytest.mark.parametrize("name", ["adaptive4", "adaptive7", "binary128"])
+def test_adjoint_dot_product(name):
+    """<v, J u> (oracle complex step at 96 sampled cells) against <J^T v, u> (GPU
+    adjoint) for v supported on those cells: on the 4-level adaptive binary, on the
+    7-level adaptive binary of the benchmark and on the 128^3 differentiation case."""
+    w = W.adaptive_binary(3, 0.08) if name == "adaptive4" else W.make(name)
     tree, rho = w.tree, w.rho.reshape(-1)
     n = rho.size
     rng = np.random.default_rng(33)

@@ -22,8 +22,10 @@ def cuda_ready():
     build.build()
 
 
-def _solve(tree, rho, precision):
+def _solve(tree, rho, precision, corr64=False):
     fmm = binding.OctoFMM(tree, 0.5, precision)
+    if corr64:
+        binding.octo_fmm_set_option(fmm.handle, 5, 1)
     r = torch.from_numpy(np.ascontiguousarray(rho.reshape(-1))).cuda()
     phi, g = fmm.forces(r)
     torch.cuda.synchronize()
@@ -90,3 +92,69 @@ def test_mixed_physical_units():
     po, go, _ = oracle.fmm(tree, w.rho)
     ephi, eg = _errs(phi, g, po, go)
     assert ephi <= TOL_MIXED and eg <= TOL_MIXED, (ephi, eg)
+
+
+def _conservation(tree, rho, g):
+    """|sum F| / sum |F| and |sum x x F| / sum |x x F| for F = m g over the leaf cells."""
+    m = rho.reshape(-1) * tree.leaf_cell_h() ** 3
+    x = tree.leaf_cell_centres()
+    F = (m[None, :] * g).T
+    tau = np.cross(x - x.mean(axis=0), F)
+    return (float(np.linalg.norm(F.sum(0)) / np.abs(F).sum()),
+            float(np.linalg.norm(tau.sum(0)) / np.abs(tau).sum()))
+
+
+@pytest.mark.parametrize("name", ["uniform16", "tiny_adaptive", "adaptive4"])
+def test_mixed_conservation_beside_fp64(name):
+    """Newton III and angular momentum (Section IV-C's angular-momentum-conserving
+    modification) on the mixed path, with the correction terms formed in float32
+    inside the float32 far-field pair (the default) and in float64 (option 5),
+    beside the float64 path and beside the oracle without the correction.
+
+    The mixed residuals sit at float32 rounding of the pair terms (~1e-10 to 1e-9
+    of sum |x x F|) in both variants; where the truncation torque that the
+    correction removes is larger (uniform16, tiny_adaptive: ~1e-6), the mixed
+    path must stay three orders of magnitude below it."""
+    if name == "uniform16":
+        w = W.uniform16(0)
+        tree, rho = w.tree, w.rho
+    elif name == "tiny_adaptive":
+        tree = W.tree_from_refined({(0, 0, 0, 0), (1, 1, 0, 0)}, 16.0)
+        rho = np.random.default_rng(12).lognormal(size=(tree.n_leaf, 512))
+    else:
+        w = W.adaptive_binary(3, 0.08)
+        tree, rho = w.tree, w.rho
+    res = {}
+    for label, precision, c64 in (("fp64", binding.OCTO_FP64, False), ("mixed", binding.OCTO_MIXED, False),
+                                  ("mixed_corr64", binding.OCTO_MIXED, True)):
+        _, g = _solve(tree, rho, precision, c64)
+        res[label] = _conservation(tree, rho, g)
+    _, g_nc, _ = oracle.fmm(tree, rho, correction=False)
+    res["oracle_no_correction"] = _conservation(tree, rho, g_nc)
+    print(name, {k: f"force {a:.2e} torque {b:.2e}" for k, (a, b) in res.items()})
+    assert res["fp64"][0] <= 1e-13 and res["fp64"][1] <= 1e-13
+    for label in ("mixed", "mixed_corr64"):
+        assert res[label][0] <= 1e-8, (label, res)
+        assert res[label][1] <= max(1e-3 * res["oracle_no_correction"][1], 1e-8), (label, res)
+
+
+@pytest.mark.parametrize("name", ["tiny_adaptive", "unbalanced", "adaptive4"])
+def test_mixed_corr64_variant_against_oracle(name):
+    """The float64-correction variant of the mixed path (option 5) meets the mixed
+    tolerance; both variants' errors are printed side by side."""
+    if name == "adaptive4":
+        w = W.adaptive_binary(3, 0.08)
+        tree, rho = w.tree, w.rho
+    else:
+        refined = {(0, 0, 0, 0), (1, 1, 0, 0)} if name == "tiny_adaptive" else \
+            {(0, 0, 0, 0), (1, 0, 0, 0), (2, 1, 1, 1), (3, 3, 3, 3)}
+        tree = W.tree_from_refined(refined, 16.0)
+        rho = np.random.default_rng(13).lognormal(size=(tree.n_leaf, 512))
+    po, go, _ = oracle.fmm(tree, rho)
+    out = {}
+    for label, c64 in (("mixed", False), ("mixed_corr64", True)):
+        phi, g = _solve(tree, rho, binding.OCTO_MIXED, c64)
+        out[label] = _errs(phi, g, po, go)
+    print(name, {k: f"phi {a:.2e} g {b:.2e}" for k, (a, b) in out.items()})
+    for label, (ephi, eg) in out.items():
+        assert ephi <= TOL_MIXED and eg <= TOL_MIXED, (label, ephi, eg)

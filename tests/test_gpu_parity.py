@@ -198,26 +198,42 @@ def test_errors_are_reported():
 @pytest.mark.parametrize("precision", [binding.OCTO_FP64, binding.OCTO_MIXED])
 def test_interaction_strategies_bit_identical(precision):
     """Per-kind launches and the persistent work queue (every register budget) run
-    the same item functions: identical results, and the autotuner picks one of them."""
+    the same item functions: identical results for every interior shape (mixed
+    precision: 32 or 64 stencil entries per float32 partial sum, half- or
+    quarter-node items), each shape within the mixed tolerance of the oracle, and
+    the autotuner picks one of the candidates."""
     w = W.adaptive_binary(3, 0.08)
     r = torch.from_numpy(w.rho.reshape(-1).copy()).cuda()
-    outs = []
-    budgets = (1, 2, 3) if precision == binding.OCTO_MIXED else (1, 2)
+    mixed = precision == binding.OCTO_MIXED
+    budgets = (1, 2, 3) if mixed else (1, 2)
+    shapes = [(32, 1), (64, 1), (32, 2), (64, 2)] if mixed else [None]
+    po, go, _ = oracle.fmm(w.tree, w.rho) if mixed else (None, None, None)
     cross = None
-    for mode, minb in [(1, 1)] + [(2, b) for b in budgets]:
-        fmm = binding.OctoFMM(w.tree, 0.5, precision)
-        binding.octo_fmm_set_option(fmm.handle, 3, mode)
-        binding.octo_fmm_set_option(fmm.handle, 4, minb)
-        phi, g = fmm.forces(r)
-        outs.append((phi.clone(), g.clone()))
-        names = _stage_names(fmm)
-        if mode == 1:
-            cross = "cross_cells" in names
-        else:  # the tabulated cross-level pairs ran as items of the persistent queue
-            assert ("cross_cells_apply" in names) == cross, names
-    assert cross  # this tree has tabulated cross-level pairs
-    for phi, g in outs[1:]:
-        assert torch.equal(phi, outs[0][0]) and torch.equal(g, outs[0][1])
+    first = None
+    for shape in shapes:
+        outs = []
+        for mode, minb in [(1, 1)] + [(2, b) for b in budgets]:
+            fmm = binding.OctoFMM(w.tree, 0.5, precision)
+            binding.octo_fmm_set_option(fmm.handle, 3, mode)
+            binding.octo_fmm_set_option(fmm.handle, 4, minb)
+            if shape is not None:
+                binding.octo_fmm_set_option(fmm.handle, 6, shape[0])
+                binding.octo_fmm_set_option(fmm.handle, 7, shape[1])
+            phi, g = fmm.forces(r)
+            outs.append((phi.clone(), g.clone()))
+            names = _stage_names(fmm)
+            if mode == 1:
+                cross = "cross_cells" in names
+            else:  # the tabulated cross-level pairs ran as items of the persistent queue
+                assert ("cross_cells_apply" in names) == cross, names
+        assert cross  # this tree has tabulated cross-level pairs
+        for phi, g in outs[1:]:
+            assert torch.equal(phi, outs[0][0]) and torch.equal(g, outs[0][1]), shape
+        if mixed:
+            p, gg = outs[0][0].cpu().numpy(), outs[0][1].cpu().numpy()
+            assert _rel_phi(p, po) <= 1e-6 and _rel_g(gg, go) <= 1e-6, shape
+        if first is None:
+            first = outs[0]
     fmm = binding.OctoFMM(w.tree, 0.5, precision)
     phi, g = fmm.forces(r)
     assert binding.octo_fmm_get_option(fmm.handle, 3) in (1, 2)
@@ -226,4 +242,9 @@ def test_interaction_strategies_bit_identical(precision):
         assert binding.octo_fmm_get_option(fmm.handle, 13) == 0
         with pytest.raises(binding.OctoError):
             binding.octo_fmm_set_option(fmm.handle, 4, 3)
-    assert torch.equal(phi, outs[0][0]) and torch.equal(g, outs[0][1])
+        assert torch.equal(phi, first[0]) and torch.equal(g, first[1])
+    else:
+        shape = (binding.octo_fmm_get_option(fmm.handle, 6), binding.octo_fmm_get_option(fmm.handle, 7))
+        assert shape in shapes
+        assert binding.octo_fmm_get_option(fmm.handle, 14) > 0 and binding.octo_fmm_get_option(fmm.handle, 15) > 0
+        assert _rel_phi(phi.cpu().numpy(), po) <= 1e-6 and _rel_g(g.cpu().numpy(), go) <= 1e-6
