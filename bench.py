@@ -159,8 +159,10 @@ def kernel_sources_sha256(read=None):
     return h.hexdigest()
 
 
-def recorded_traffic(stage: str, workload: str):
-    """(bytes per launch, source) of a matching capture, or (None, reason)."""
+def recorded_traffic(stage: str, workload: str, shape=None, blocks=None):
+    """(bytes per launch, source) of a matching capture, or (None, reason).  shape
+    (entries per float32 partial, split) and blocks (register budget) must match the
+    capture's when both are known."""
     try:
         with open(TRAFFIC_FILE) as f:
             entries = json.load(f)["entries"]
@@ -169,9 +171,13 @@ def recorded_traffic(stage: str, workload: str):
     sha = kernel_sources_sha256()
     for e in entries:
         if e["stage"] == stage and e["workload"] == workload:
-            if e["sources_sha256"] == sha:
-                return int(e["bytes"]), e["command"]
-            return None, "kernel changed since the capture"
+            if e["sources_sha256"] != sha:
+                return None, "kernel changed since the capture"
+            if shape is not None and e.get("interior_shape") is not None and list(shape) != e["interior_shape"]:
+                return None, "the capture is of another interior shape"
+            if blocks is not None and e.get("blocks_per_sm") is not None and blocks != e["blocks_per_sm"]:
+                return None, "the capture is of another register budget"
+            return int(e["bytes"]), e["command"]
     return None, "no capture for this kernel and workload"
 
 
@@ -454,7 +460,9 @@ def run_ours(args):
     # dominant kernel of the step and its roofline
     mean_stage = stage_ms.mean(axis=0)
     roof = roofline_of(info, mean_stage, _measured_peaks(), alu)
-    roof["traffic"], roof["traffic_source"] = recorded_traffic(roof["kernel"], w.name)
+    gopt = lambda k: binding.octo_fmm_get_option(fmm.handle, k)  # noqa: E731
+    shape = (gopt(6), gopt(7)) if precision == binding.OCTO_MIXED else None
+    roof["traffic"], roof["traffic_source"] = recorded_traffic(roof["kernel"], w.name, shape, gopt(4))
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     nlc = fmm.n_leaf_cells
@@ -476,7 +484,6 @@ def run_ours(args):
 
     # the float64 path on the same workload, for the mixed-vs-float64 comparison
     fp64 = None
-    gopt = lambda k: binding.octo_fmm_get_option(fmm.handle, k)  # noqa: E731
     strategy = {"chosen": {1: "per-kind launches", 2: "persistent work queue"}[gopt(3)],
                 "register_budget_blocks_per_sm": gopt(4),
                 "autotune_us": {"per_kind": gopt(10), "persistent_1": gopt(11), "persistent_2": gopt(12),
@@ -553,6 +560,90 @@ def run_ours(args):
     return 0
 
 
+def run_oracle_timing(args):
+    """Full (unsampled) oracle solves of the small configurations on the host cores,
+    at all cores and at one thread: 16^3 lognormal (seeds 0-2), the 64^3 binary and
+    the ~1e3-leaf adaptive sweep tree; cell-interactions/s from the interactions the
+    oracle evaluated.  One JSON line; no GPU is used."""
+    import oracle
+    from paper_2304_11002_gb300 import workloads as W
+    cases = [("uniform16_s0", lambda: W.uniform16(0)), ("uniform16_s1", lambda: W.uniform16(1)),
+             ("uniform16_s2", lambda: W.uniform16(2)), ("binary64", W.binary64),
+             ("sweep1000_q0.7_s0", lambda: W.sweep(1000, q=0.7, seed=0))]
+    all_cores = oracle.set_threads(0)
+    out = {"kind": "oracle", "cpu_model": cpu_model(), "cores": all_cores, "unit": METRIC, "runs": []}
+    for name, make in cases:
+        w = make()
+        for threads in (all_cores, 1):
+            if threads == 1 and name not in args.oracle_one_thread:
+                continue
+            oracle.set_threads(threads)
+            work = np.zeros(1, np.int64)
+            t0 = time.perf_counter()
+            oracle.fmm(w.tree, w.rho, w.theta, work=work)
+            dt = time.perf_counter() - t0
+            out["runs"].append({"config": name, "threads": threads, "interactions": int(work[0]), "seconds": dt,
+                                "value": float(work[0]) / dt})
+            print(json.dumps(out["runs"][-1]), file=sys.stderr, flush=True)
+    oracle.set_threads(all_cores)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_backward(args):
+    """The hand-written adjoint alone: d(loss)/d(rho) for random d(loss)/d(phi) and
+    d(loss)/d(g) after one float64 forward solve, timed over the steps with CUDA
+    events (L2 flushed before every step).  One JSON line; value = the solve's
+    ordered interactions per second of adjoint time."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2304_11002_gb300 import binding, build
+    from paper_2304_11002_gb300 import workloads as W
+    build.build()
+    w = W.make(args.workload)
+    n_inter = counts_total(w)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    alu = NOMINAL_ALU if args.nominal_peaks else measure_alu_peaks(0, stream)
+    fmm = binding.OctoFMM(w.tree, w.theta, binding.OCTO_FP64)
+    nlc = fmm.n_leaf_cells
+    rho = torch.from_numpy(np.ascontiguousarray(w.rho.reshape(-1))).cuda()
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    dphi = torch.randn(nlc, dtype=torch.float64, device="cuda", generator=gen)
+    dg = torch.randn((3, nlc), dtype=torch.float64, device="cuda", generator=gen)
+    drho = torch.empty(nlc, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        fmm.forces(rho, stream=stream)
+        for _ in range(args.warmup):
+            binding.octo_fmm_backward(fmm.handle, dphi, dg, drho, stream)
+        stream.synchronize()
+        ms = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                e0.record(stream)
+                binding.octo_fmm_backward(fmm.handle, dphi, dg, drho, stream)
+                e1.record(stream)
+                stream.synchronize()
+                ms.append(e0.elapsed_time(e1))
+    binding.octo_fmm_stats(fmm.handle)  # raises on a failed device-side check
+    t = float(np.mean(ms))
+    f64 = binding.octo_fmm_get_option(fmm.handle, 24)  # counted float64 flops of one backward
+    line = {"metric": "adjoint " + METRIC, "value": n_inter / (t / 1e3), "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "note": w.note, "theta": w.theta, "order": 3,
+                       "step": "octo_fmm_backward after one float64 forward solve",
+                       "l2": "flushed before every timed step"},
+            "roofline": {"bound": "alu", "pipe": "fp64", "achieved": f64 / (t / 1e3) / 1e12, "peak": alu["fp64"],
+                         "unit": "TFLOP/s", "frac": f64 / (t / 1e3) / 1e12 / alu["fp64"],
+                         "flops_per_step": f64, "peak_source": alu["source"]},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -566,6 +657,12 @@ def main():
     ap.add_argument("--interior-shape", type=int, nargs=2, metavar=("CHUNK", "SPLIT"), default=None,
                     help="mixed precision: fix the interior shape (32|64 entries per float32 partial, "
                          "1|2 = half|quarter-node items) instead of autotuning it")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="full oracle solves of the small configurations on the host cores (no GPU)")
+    ap.add_argument("--oracle-one-thread", nargs="*", default=["uniform16_s0", "binary64"],
+                    help="configurations of --oracle-timing also timed on one thread")
+    ap.add_argument("--backward-only", action="store_true",
+                    help="time the float64 adjoint (octo_fmm_backward) alone on the workload")
     ap.add_argument("--corr64", action="store_true",
                     help="mixed precision with the angular-momentum correction in float64 (per-kind launches)")
     ap.add_argument("--nominal-peaks", action="store_true",
@@ -583,6 +680,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.backward_only:
+        return run_backward(args)
+    if args.oracle_timing:
+        return run_oracle_timing(args)
     return run_ours(args)
 
 

@@ -20,10 +20,11 @@
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute calls are
  *    asynchronous: they enqueue work and return.  Launch and argument errors are
  *    returned immediately.  Errors found on the device (a density that is not
- *    finite and positive, a failed index check of the adjoint) are recorded in a
- *    device word of the handle and reported, once, by the next octo_fmm_stats call
- *    or by octo_fmm_forces_host, which read it back.  No kernel of this library
- *    waits on another block, kernel or device.
+ *    finite and positive, a bounded wait of a kernel for its own bulk copies that
+ *    ran out, a failed index check of the adjoint) are recorded in a device word of
+ *    the handle and reported, once, by the next octo_fmm_stats call or by
+ *    octo_fmm_forces_host, which read it back.  No kernel of this library waits on
+ *    another block, kernel or device.
  *  - Return value: OCTO_OK (0) or a negative OCTO_E* status; octo_fmm_last_error()
  *    gives a message.  No C++ exception crosses this interface.
  *  - One handle is not thread-safe; use one handle per host thread or serialise.
@@ -62,7 +63,7 @@ enum {
   OCTO_ETREE = -2,    /* inconsistent octree descriptor */
   OCTO_ENOMEM = -3,   /* device or host allocation failed */
   OCTO_ECUDA = -4,    /* a CUDA runtime call failed */
-  OCTO_ETIMEOUT = -5, /* reserved: no call of this library waits on the device */
+  OCTO_ETIMEOUT = -5, /* a kernel's bounded wait for its own asynchronous copies ran out */
   OCTO_ENONPOS = -6,  /* a leaf density was not finite and positive (NaN, <= 0, inf) */
   OCTO_ESTATE = -7    /* call out of order (e.g. backward before a forward solve) */
 };
@@ -128,8 +129,9 @@ int octo_fmm_backward(octo_fmm_t h, const double* dphi_dev, const double* dg_dev
 /* Ordered interaction counts of the plan: counts[0] same-level M2L, counts[1]
  * cross-level M2L, counts[2] same-level P2P, counts[3] cross-level P2P.
  * Synchronises the device and reports a pending device-side error, then clears it:
- * OCTO_ENONPOS for a density that was not finite and positive, OCTO_ECUDA for a
- * failed index check of the adjoint (counts are filled in either case). */
+ * OCTO_ENONPOS for a density that was not finite and positive, OCTO_ETIMEOUT for a
+ * bounded wait that ran out, OCTO_ECUDA for a failed index check of the adjoint
+ * (counts are filled in either case). */
 int octo_fmm_stats(octo_fmm_t h, int64_t counts[4]);
 
 /* Host-only planning: validates the tree and returns the counts above without
@@ -181,7 +183,10 @@ int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value);
  * autotuner's shape candidates (chunk 64, quarter-node items; 0 when not
  * measured).  Sizes of the handle (read-only): key 20 = leaf cells
  * (n_leaf*512, the length of rho and phi), 21 = CUDA device the handle was created
- * on, 22 = octree nodes, 23 = precision (OCTO_FP64 or OCTO_MIXED). */
+ * on, 22 = octree nodes, 23 = precision (OCTO_FP64 or OCTO_MIXED), 24 = algorithmic
+ * float64 flops of one octo_fmm_backward over its interaction pairs (each pair
+ * expression's reverse mode as written, a fused multiply-add counting two; the
+ * tree passes are not counted). */
 int octo_fmm_get_option(octo_fmm_t h, int key, int64_t* value);
 
 /* Number of kernel launches one octo_fmm_forces call enqueues. */

@@ -14,6 +14,7 @@
 
 #include "../../include/octo_fmm.h"
 #include "kernels.h"
+#include "pair_vjp.cuh"
 #include "plan.h"
 
 using namespace octo;
@@ -245,6 +246,15 @@ struct Counted {
   HD friend Counted operator+(Counted a, Counted b) { tick(); return Counted(a.v + b.v); }
   HD friend Counted operator-(Counted a, Counted b) { tick(); return Counted(a.v - b.v); }
   HD friend Counted operator*(Counted a, Counted b) { tick(); return Counted(a.v * b.v); }
+  HD friend Counted operator/(Counted a, Counted b) { tick(); return Counted(a.v / b.v); }
+  HD friend Counted sqrt(Counted a) {
+    tick();
+#ifndef __CUDA_ARCH__
+    return Counted(std::sqrt(a.v));
+#else
+    return Counted(::sqrt(a.v));
+#endif
+  }
   HD Counted operator-() const { return Counted(-v); }
   HD Counted& operator+=(Counted b) { tick(); v += b.v; return *this; }
   HD Counted& operator-=(Counted b) { tick(); v -= b.v; return *this; }
@@ -264,6 +274,18 @@ int64_t m2l_pair_flops() {
   return g_counted_ops + 3 + 5 + 8;
 }
 constexpr int64_t kConvFlopsPerPair = 8;  // four fused multiply-adds
+
+// One reverse-mode pair (pair_vjp.cuh) as written, with the host's 1/sqrt for
+// the reciprocal square root (the device refines a float32 seed instead: 8 more).
+template <bool FULL, bool TOCT, bool SRC, bool OH>
+int64_t vjp_flops() {
+  Counted Q[6], O[10], Oh[10], Lb[23];
+  PairVJPT<Counted> g;
+  g_counted_ops = 0;
+  m2l_pair_vjp<FULL, TOCT, SRC, OH, Counted>(Counted(1.0), Counted(2.0), Counted(3.0), Counted(1.0), Q, O, Oh, Lb,
+                                             g);
+  return g_counted_ops - 2 + 8;
+}
 // near offsets run as (d, -d) pairs: one add, one subtract and four fused
 // multiply-adds per two pairs
 constexpr int64_t kNearFlopsPer2Pairs = 2 + 4 * 2;
@@ -699,8 +721,9 @@ int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
 }
 
 // Reports the device error word read back as `err` (OCTO_ENONPOS for a density
-// that was not finite and positive, else OCTO_ECUDA for a failed index check of
-// the adjoint) and clears it, so that each error is reported once.
+// that was not finite and positive, OCTO_ETIMEOUT for a bounded wait that ran out,
+// else OCTO_ECUDA for a failed index check of the adjoint) and clears it, so that
+// each error is reported once.
 int report_device_errors(octo_fmm* h, int err, cudaStream_t s) {
   if (!err) return OCTO_OK;
   cudaError_t e = cudaMemsetAsync(h->d_err, 0, sizeof(int), s);
@@ -708,6 +731,8 @@ int report_device_errors(octo_fmm* h, int err, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(h, e, "clear the device error word");
   if (err & kErrDensity)
     return fail(h, OCTO_ENONPOS, "the density of a leaf cell was not finite and positive (NaN, <= 0 or inf)");
+  if (err & kErrTimeout)
+    return fail(h, OCTO_ETIMEOUT, "a kernel's bounded wait for its own asynchronous copies ran out; results incomplete");
   return fail(h, OCTO_ECUDA, "a device-side index check failed (bits " + std::to_string(err) + ")");
 }
 
@@ -1195,6 +1220,22 @@ int octo_fmm_get_option(octo_fmm_t h, int key, int64_t* value) {
     case 11:
     case 12:
     case 13: *value = (int64_t)(1000.0f * h->tune_ms[key - 10]); return OCTO_OK;
+    case 24: {
+      // algorithmic float64 flops of one octo_fmm_backward over its pair kinds: every
+      // same-level M2L pair twice (as target: centre and octupole adjoints; as
+      // source: centre, mass and moments), leaf-leaf and tabulated cross-level pairs
+      // (4 fused multiply-adds each), the general cross-level lists likewise; the
+      // tree passes (L2L, M2M, P2M, L2P transposes) are not counted
+      const Plan& P = h->plan;
+      const int64_t a = vjp_flops<true, true, false, true>(), bf = vjp_flops<true, true, true, false>(),
+                    bl = vjp_flops<false, false, true, false>();
+      int64_t f = P.kernel_pairs[0] * (a + bf) + P.kernel_pairs[3] * bl;
+      f += (P.kernel_pairs[1] + P.kernel_pairs[2] + P.xc_pairs) * kConvFlopsPerPair;
+      f += (h->xg.f_pairs - h->xg.f_p2p) * (a + bf) + (h->xg.l_pairs - h->xg.l_p2p) * bl;
+      f += (h->xg.f_p2p + h->xg.l_p2p) * 2 * kP2PFlopsPerPair;
+      *value = f;
+      return OCTO_OK;
+    }
     case 20: *value = h->n_leaf_cells(); return OCTO_OK;
     case 21: *value = h->device; return OCTO_OK;
     case 22: *value = h->plan.n_nodes; return OCTO_OK;

@@ -595,6 +595,14 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
       tma::mbar_wait(bar + (b & 1), (b >> 1) & 1);
       if (b + 1 < nblk) tma::mbar_wait(bar + ((b + 1) & 1), ((b + 1) >> 1) & 1);
     }
+    // every phase of both barriers has completed: invalidate them, so that the next
+    // leaf item of this block can initialise them again and other items may reuse
+    // the memory
+    __syncwarp();
+    if (lane == 0) {
+      tma::mbar_inval(bar);
+      tma::mbar_inval(bar + 1);
+    }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       L0[q] = f[q][0].value() * ih;

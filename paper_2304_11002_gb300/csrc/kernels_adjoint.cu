@@ -249,12 +249,53 @@ __device__ __forceinline__ void general_partners(const DevTree& t, const Stencil
 }
 
 // Cell X of an interior node: every stencil partner Y; cell X of a leaf node: the
-// partners in refined neighbour nodes.  Two passes over the partners keep the live
-// state small: (a) X as target of (X <- Y) gives the gradients for X's centre and
-// octupole (through Oh = O / m); (b) X as source of (Y <- X) gives those for X's
-// centre, mass and moments.  Leaf cells keep only the mass gradient.
-__global__ void __launch_bounds__(128) k_adj_general(DevTree t, const int* __restrict__ nodes, Stencils st,
-                                                     AdjState as) {
+// partners in refined neighbour nodes.  Two kernels, one per role of X, keep the
+// live state of each small: (a) X as target of (X <- Y) gives the gradients for X's
+// centre and octupole (through Oh = O / m), interior X only; (b) X as source of
+// (Y <- X) gives those for X's centre, mass and moments (leaf cells keep only the
+// mass gradient).  Each kernel adds into the adjoints of the cells it owns, (a)
+// before (b).
+__global__ void __launch_bounds__(128) k_adj_general_target(DevTree t, const int* __restrict__ nodes, Stencils st,
+                                                            AdjState as) {
+  const int node = nodes[blockIdx.x >> 2];
+  int* err = as.err;
+  ADJ_RETURN_UNLESS(node >= 0 && node < t.n_nodes, 8);
+  if (t.children[8 * node] < 0) return;  // leaf cells carry no octupole: nothing to do as target
+  int p, a, b, c;
+  parity_cell_a((blockIdx.x & 3) * 2, threadIdx.x, p, a, b, c);
+  const int lvl = t.level[node];
+  const int64_t NC = t.NC;
+  const int64_t X = (int64_t)node * 512 + a + 8 * b + 64 * c;
+  const double* mp = as.mp;
+  const double mX = mp[X];
+  const double XX0 = mp[(F_X + 0) * NC + X], XX1 = mp[(F_X + 1) * NC + X], XX2 = mp[(F_X + 2) * NC + X];
+  double gX[3] = {0, 0, 0}, gm = 0;
+  const double inv_m = 1.0 / mX;
+  double OhX[10], LbX[23], gOh[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < 10; ++i) OhX[i] = mp[(F_O + i) * NC + X] * inv_m;
+  load_lb(as.locb, NC, X, true, LbX);
+  general_partners(t, st, node, lvl, p, a, b, c, false, err, [&](int64_t Y, bool) {
+    double QY[6], OY[10];
+    const double mY = mp[Y];
+    const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
+    for (int i = 0; i < 6; ++i) QY[i] = mp[(F_Q + i) * NC + Y];
+    for (int i = 0; i < 10; ++i) OY[i] = mp[(F_O + i) * NC + Y];
+    PairVJP g;
+    m2l_pair_vjp<true, true, false, true>(R0, R1, R2, mY, QY, OY, OhX, LbX, g);
+    for (int f = 0; f < 3; ++f) gX[f] += g.R[f];
+    for (int i = 0; i < 10; ++i) gOh[i] += g.Oh[i];
+  });
+  // Oh = O * (1 / m)
+  for (int i = 0; i < 10; ++i) {
+    as.mpb[(F_O + i) * NC + X] += gOh[i] * inv_m;
+    gm -= gOh[i] * OhX[i] * inv_m;
+  }
+  for (int f = 0; f < 3; ++f) as.mpb[(F_X + f) * NC + X] += gX[f];
+  as.mpb[X] += gm;
+}
+
+__global__ void __launch_bounds__(128) k_adj_general_source(DevTree t, const int* __restrict__ nodes, Stencils st,
+                                                            AdjState as) {
   const int node = nodes[blockIdx.x >> 2];
   int* err = as.err;
   ADJ_RETURN_UNLESS(node >= 0 && node < t.n_nodes, 8);
@@ -268,56 +309,33 @@ __global__ void __launch_bounds__(128) k_adj_general(DevTree t, const int* __res
   const double mX = mp[X];
   const double XX0 = mp[(F_X + 0) * NC + X], XX1 = mp[(F_X + 1) * NC + X], XX2 = mp[(F_X + 2) * NC + X];
   double gX[3] = {0, 0, 0}, gm = 0;
-  if (!xleaf) {  // (a) X <- Y
-    const double inv_m = 1.0 / mX;
-    double OhX[10], LbX[23], gOh[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < 10; ++i) OhX[i] = mp[(F_O + i) * NC + X] * inv_m;
-    load_lb(as.locb, NC, X, true, LbX);
-    general_partners(t, st, node, lvl, p, a, b, c, false, err, [&](int64_t Y, bool) {
-      double QY[6], OY[10];
-      const double mY = mp[Y];
-      const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
-      for (int i = 0; i < 6; ++i) QY[i] = mp[(F_Q + i) * NC + Y];
-      for (int i = 0; i < 10; ++i) OY[i] = mp[(F_O + i) * NC + Y];
-      PairVJP g;
-      m2l_pair_vjp<true, true, false, true>(R0, R1, R2, mY, QY, OY, OhX, LbX, g);
-      for (int f = 0; f < 3; ++f) gX[f] += g.R[f];
-      for (int i = 0; i < 10; ++i) gOh[i] += g.Oh[i];
-    });
-    // Oh = O * (1 / m)
-    for (int i = 0; i < 10; ++i) {
-      as.mpb[(F_O + i) * NC + X] += gOh[i] * inv_m;
-      gm -= gOh[i] * OhX[i] * inv_m;
+  // Y <- X, R_YX = -R
+  double QX[6], OX[10], gQ[6] = {0, 0, 0, 0, 0, 0}, gO[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < 6; ++i) QX[i] = mp[(F_Q + i) * NC + X];
+  for (int i = 0; i < 10; ++i) OX[i] = mp[(F_O + i) * NC + X];
+  general_partners(t, st, node, lvl, p, a, b, c, xleaf, err, [&](int64_t Y, bool yleaf) {
+    const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
+    double LbY[23];
+    PairVJP g;
+    if (yleaf) {
+      load_lb(as.locb, NC, Y, false, LbY);
+      m2l_pair_vjp<false, false, true, false>(-R0, -R1, -R2, mX, QX, OX, nullptr, LbY, g);
+    } else {
+      double OhY[10];
+      const double inv_mY = 1.0 / mp[Y];
+      for (int i = 0; i < 10; ++i) OhY[i] = mp[(F_O + i) * NC + Y] * inv_mY;
+      load_lb(as.locb, NC, Y, true, LbY);
+      m2l_pair_vjp<true, true, true, false>(-R0, -R1, -R2, mX, QX, OX, OhY, LbY, g);
     }
-  }
-  {  // (b) Y <- X, R_YX = -R
-    double QX[6], OX[10], gQ[6] = {0, 0, 0, 0, 0, 0}, gO[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < 6; ++i) QX[i] = mp[(F_Q + i) * NC + X];
-    for (int i = 0; i < 10; ++i) OX[i] = mp[(F_O + i) * NC + X];
-    general_partners(t, st, node, lvl, p, a, b, c, xleaf, err, [&](int64_t Y, bool yleaf) {
-      const double R0 = XX0 - mp[(F_X + 0) * NC + Y], R1 = XX1 - mp[(F_X + 1) * NC + Y], R2 = XX2 - mp[(F_X + 2) * NC + Y];
-      double LbY[23];
-      PairVJP g;
-      if (yleaf) {
-        load_lb(as.locb, NC, Y, false, LbY);
-        m2l_pair_vjp<false, false, true, false>(-R0, -R1, -R2, mX, QX, OX, nullptr, LbY, g);
-      } else {
-        double OhY[10];
-        const double inv_mY = 1.0 / mp[Y];
-        for (int i = 0; i < 10; ++i) OhY[i] = mp[(F_O + i) * NC + Y] * inv_mY;
-        load_lb(as.locb, NC, Y, true, LbY);
-        m2l_pair_vjp<true, true, true, false>(-R0, -R1, -R2, mX, QX, OX, OhY, LbY, g);
-      }
-      for (int f = 0; f < 3; ++f) gX[f] -= g.R[f];
-      gm += g.m;
-      for (int i = 0; i < 6; ++i) gQ[i] += g.Q[i];
-      for (int i = 0; i < 10; ++i) gO[i] += g.O[i];
-    });
-    if (!xleaf) {
-      for (int f = 0; f < 3; ++f) as.mpb[(F_X + f) * NC + X] += gX[f];
-      for (int i = 0; i < 6; ++i) as.mpb[(F_Q + i) * NC + X] += gQ[i];
-      for (int i = 0; i < 10; ++i) as.mpb[(F_O + i) * NC + X] += gO[i];
-    }
+    for (int f = 0; f < 3; ++f) gX[f] -= g.R[f];
+    gm += g.m;
+    for (int i = 0; i < 6; ++i) gQ[i] += g.Q[i];
+    for (int i = 0; i < 10; ++i) gO[i] += g.O[i];
+  });
+  if (!xleaf) {
+    for (int f = 0; f < 3; ++f) as.mpb[(F_X + f) * NC + X] += gX[f];
+    for (int i = 0; i < 6; ++i) as.mpb[(F_Q + i) * NC + X] += gQ[i];
+    for (int i = 0; i < 10; ++i) as.mpb[(F_O + i) * NC + X] += gO[i];
   }
   as.mpb[X] += gm;
 }
@@ -507,7 +525,7 @@ cudaError_t adjoint_local_bytes(size_t* out) {
   size_t m = 0;
   cudaFuncAttributes fa;
   const void* fns[] = {(const void*)k_adj_seed,         (const void*)k_adj_l2l,         (const void*)k_adj_conv,
-                       (const void*)k_adj_general,      (const void*)k_adj_cross<true>, (const void*)k_adj_cross<false>,
+                       (const void*)k_adj_general_target, (const void*)k_adj_general_source, (const void*)k_adj_cross<true>, (const void*)k_adj_cross<false>,
                        (const void*)k_adj_m2m,          (const void*)k_adj_p2m};
   for (const void* f : fns) {
     cudaError_t e = cudaFuncGetAttributes(&fa, f);
@@ -528,7 +546,10 @@ cudaError_t launch_backward(const DevTree& t, const BackwardArgs& ba, cudaStream
     if (n > 0) k_adj_l2l<<<2 * n, 256, 0, s>>>(t, ba.level_start[l], as);
   }
   if (ba.n_leaf_nodes) k_adj_conv<<<2 * ba.n_leaf_nodes, 256, 0, s>>>(t, ba.leaf_nodes, ba.st, as);
-  if (ba.n_general) k_adj_general<<<4 * ba.n_general, 128, 0, s>>>(t, ba.general_nodes, ba.st, as);
+  if (ba.n_general) {
+    k_adj_general_target<<<4 * ba.n_general, 128, 0, s>>>(t, ba.general_nodes, ba.st, as);
+    k_adj_general_source<<<4 * ba.n_general, 128, 0, s>>>(t, ba.general_nodes, ba.st, as);
+  }
   if (ba.xf.n_targets) k_adj_cross<true><<<(ba.xf.n_targets + 127) / 128, 128, 0, s>>>(t, ba.xf, as);
   if (ba.xl.n_targets) k_adj_cross<false><<<(ba.xl.n_targets + 127) / 128, 128, 0, s>>>(t, ba.xl, as);
   e = launch_cross_cells_adjoint(t, ba.xc, ba.locb, ba.mpb, ba.xc_grid, s);

@@ -12,7 +12,9 @@
 namespace octo {
 namespace tma {
 
-constexpr int kWaitLimit = 1 << 20;
+// A 640-byte copy lands within microseconds; 65536 polls (each may suspend the
+// thread briefly) bound a wait to well under a second.
+constexpr int kWaitLimit = 1 << 16;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -21,6 +23,13 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 // One arrival per phase (the issuing thread's arrive.expect_tx).
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Invalidates a barrier whose phases have all completed, so that its shared memory
+// can be initialised again (or used for anything else): re-initialising a valid
+// mbarrier is undefined.
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // Makes initialised barriers visible to the asynchronous proxy (the copy engine).

@@ -29,6 +29,7 @@ def _solve(tree, rho, precision, corr64=False):
     r = torch.from_numpy(np.ascontiguousarray(rho.reshape(-1))).cuda()
     phi, g = fmm.forces(r)
     torch.cuda.synchronize()
+    binding.octo_fmm_stats(fmm.handle)  # raises on a device-side error (e.g. a bounded wait that ran out)
     return phi.cpu().numpy(), g.cpu().numpy()
 
 

@@ -32,6 +32,7 @@ def _run(tree, rho, precision=binding.OCTO_FP64, theta=0.5, graph=True):
     r = torch.from_numpy(np.ascontiguousarray(rho.reshape(-1))).cuda()
     phi, g = fmm.forces(r)
     torch.cuda.synchronize()
+    binding.octo_fmm_stats(fmm.handle)  # raises on a device-side error (e.g. a bounded wait that ran out)
     return fmm, phi.cpu().numpy(), g.cpu().numpy()
 
 
