@@ -240,6 +240,44 @@ int octo_fmm_stage_times(octo_fmm_t h, float* ms, int cap);
 int octo_fmm_subgrids_noalloc(int n_subgrids, const double* rho_dev, double h, double* phi_dev, double* g_dev,
                               void* stream);
 
+/* Self-consistent-field (SCF) initial models of a synchronously rotating binary of
+ * two polytropes (Section IV-C: the binary models are initialised by an iterative
+ * SCF technique; the hydrostatic equilibrium equation in the rotating frame,
+ * integrated, is an algebraic relation between the effective potential and the
+ * enthalpy).  Inside star i: H + Phi - Omega^2 w^2 / 2 = C_i with the enthalpy
+ * H = (n + 1) K rho^(1/n) and w the distance from the rotation axis (parallel to z,
+ * through the centre of mass).  The constants Omega^2, C_1, C_2 follow from H = 0
+ * at three surface cells. */
+typedef struct {
+  double n;                        /* polytropic index of both stars, > 0 */
+  double rho_max[2];               /* the maximum density each star keeps, > 0 */
+  double rho_floor;                /* density outside the stars, >= 0 */
+  int64_t cell_a, cell_b, cell_c;  /* leaf cells (indices into rho, 0 <= i < n_leaf*512) on
+                                      the surfaces: A and B of star 1 (at different distances
+                                      from the axis), C of star 2 */
+  double x_split;                  /* cells whose centre has x < x_split belong to star 1 */
+} octo_scf_params;
+
+/* One SCF step.  phi_dev: the potential of the density in rho_dev (e.g. from
+ * octo_fmm_forces).  rho_dev is overwritten with the new density:
+ * rho = rho_max_i (H / H_max_i)^n + rho_floor where H > 0, else rho_floor.  stats
+ * (host, 8 doubles, may be NULL): Omega^2, C_1, C_2, max |rho_new - rho| /
+ * max(rho_max), and of the state that produced phi: W = sum m phi / 2, T =
+ * Omega^2 sum m w^2 / 2, Pi = sum P h^3 (P = K_i rho^(1 + 1/n), K_i from H_max_i),
+ * and the virial error |2T + W + 3 Pi| / |W|.  Synchronises the stream.  The
+ * first call allocates a small device scratch.  Errors: OCTO_EINVAL (bad
+ * parameters, cell indices out of range), OCTO_ENOMEM, OCTO_ECUDA. */
+int octo_fmm_scf_step(octo_fmm_t h, const octo_scf_params* p, double* rho_dev, const double* phi_dev, double* stats,
+                      void* stream);
+
+/* The SCF iteration: octo_fmm_forces on rho_dev, then octo_fmm_scf_step, repeated
+ * until the largest density change (stats[3]) is below tol or max_iter steps ran.
+ * rho_dev: initial guess in, equilibrium out.  history (host, may be NULL):
+ * [max_iter][8] stats of every step; *n_iter (may be NULL) receives the number of
+ * steps.  The potential uses the handle's own buffers. */
+int octo_fmm_scf_solve(octo_fmm_t h, const octo_scf_params* p, double* rho_dev, int max_iter, double tol,
+                       double* history, int* n_iter, void* stream);
+
 /* Measured arithmetic peak of the current device, the denominator of the solver's
  * roofline fractions (the paper has no counterpart; the interaction kernels are
  * bound by the float64 and float32 fused multiply-add pipes, Section VII-C's

@@ -29,7 +29,7 @@ SYMBOLS = ["octo_fmm_create", "octo_fmm_upward", "octo_fmm_interact", "octo_fmm_
            "octo_fmm_read_state", "octo_fmm_set_option", "octo_fmm_get_option", "octo_fmm_launches_per_solve",
            "octo_fmm_stage_count",
            "octo_fmm_stage_info", "octo_fmm_stage_times", "octo_fmm_subgrids_noalloc", "octo_fmm_measure_peak",
-           "octo_fmm_last_error", "octo_fmm_destroy"]
+           "octo_fmm_scf_step", "octo_fmm_scf_solve", "octo_fmm_last_error", "octo_fmm_destroy"]
 
 
 class OctoError(RuntimeError):
@@ -42,6 +42,12 @@ class TreeDesc(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("level", ctypes.POINTER(ctypes.c_int32)),
                 ("ijk", ctypes.POINTER(ctypes.c_int32)), ("children", ctypes.POINTER(ctypes.c_int32)),
                 ("origin", ctypes.c_double * 3), ("extent", ctypes.c_double)]
+
+
+class ScfParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_double), ("rho_max", ctypes.c_double * 2), ("rho_floor", ctypes.c_double),
+                ("cell_a", ctypes.c_int64), ("cell_b", ctypes.c_int64), ("cell_c", ctypes.c_int64),
+                ("x_split", ctypes.c_double)]
 
 
 _lib = None
@@ -75,6 +81,9 @@ def lib() -> ctypes.CDLL:
         L.octo_fmm_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
         L.octo_fmm_subgrids_noalloc.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, vp]
         L.octo_fmm_measure_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
+        L.octo_fmm_scf_step.argtypes = [vp, ctypes.POINTER(ScfParams), dp, dp, ctypes.POINTER(ctypes.c_double), vp]
+        L.octo_fmm_scf_solve.argtypes = [vp, ctypes.POINTER(ScfParams), dp, ctypes.c_int, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), vp]
         L.octo_fmm_last_error.argtypes = [vp]
         L.octo_fmm_last_error.restype = ctypes.c_char_p
         L.octo_fmm_destroy.argtypes = [vp]
@@ -228,6 +237,37 @@ def octo_fmm_measure_peak(fp64: bool, stream=None) -> float:
     v = ctypes.c_double()
     _check(lib().octo_fmm_measure_peak(1 if fp64 else 0, ctypes.byref(v), _stream(stream)))
     return float(v.value)
+
+
+SCF_STATS = ("omega2", "c1", "c2", "max_change", "W", "T", "Pi", "virial_error")
+
+
+def _scf_params(p: dict) -> ScfParams:
+    return ScfParams(float(p["n"]), (ctypes.c_double * 2)(*[float(v) for v in p["rho_max"]]), float(p["rho_floor"]),
+                     int(p["cell_a"]), int(p["cell_b"]), int(p["cell_c"]), float(p["x_split"]))
+
+
+def octo_fmm_scf_step(h, params: dict, rho, phi, stream=None) -> np.ndarray:
+    """One SCF step on the device: rho (overwritten) and its potential phi; returns the
+    8 statistics named in SCF_STATS."""
+    n, dev = _sizes(h)
+    prm = _scf_params(params)
+    st = (ctypes.c_double * 8)()
+    _check(lib().octo_fmm_scf_step(h, ctypes.byref(prm), _buf(rho, n, dev, "rho"), _buf(phi, n, dev, "phi"), st,
+                                   _stream(stream)), h)
+    return np.array(st[:], dtype=np.float64)
+
+
+def octo_fmm_scf_solve(h, params: dict, rho, max_iter: int, tol: float, stream=None) -> np.ndarray:
+    """The SCF iteration on the device (rho: initial guess in, equilibrium out); returns
+    the statistics of every step, [steps, 8]."""
+    n, dev = _sizes(h)
+    prm = _scf_params(params)
+    hist = (ctypes.c_double * (8 * max(int(max_iter), 1)))()
+    it = ctypes.c_int(0)
+    _check(lib().octo_fmm_scf_solve(h, ctypes.byref(prm), _buf(rho, n, dev, "rho"), int(max_iter), float(tol), hist,
+                                    ctypes.byref(it), _stream(stream)), h)
+    return np.array(hist[:8 * it.value], dtype=np.float64).reshape(it.value, 8)
 
 
 def octo_fmm_get_option(h, key: int) -> int:

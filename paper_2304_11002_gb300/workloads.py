@@ -421,3 +421,30 @@ def make(name: str, **kw) -> Workload:
     if name.startswith("star"):
         return star(int(name[4:]), **kw)
     return RECIPES[name](**kw)
+
+
+def scf_binary(name: str = "binary32"):
+    """Initial guess and surface cells of an SCF run on one of the uniform binaries:
+    (workload, params) with params as octo_scf_params takes them (n = 1.5; each star
+    keeps the maximum density of its initial polytrope; surface cells A, B = the
+    cells nearest to the outer and inner edge of star 1 on the line through both
+    centres, C = nearest to the inner edge of star 2; x_split = midway between the
+    inner edges)."""
+    scale = {"binary32": 0.5, "binary64": 1.0, "binary128": 2.0}[name]
+    w = {"binary32": binary32, "binary64": binary64, "binary128": binary128}[name]()
+    extent = float(w.tree.extent)
+    mid = extent / 2.0 + 0.5
+    sep, r1, r2 = 30.0 * scale, 12.0 * scale, 10.0 * scale
+    c1, c2 = mid - sep / 2, mid + sep / 2
+    x = w.tree.leaf_cell_centres()
+
+    def nearest(px):
+        return int(np.argmin(np.linalg.norm(x - np.array([px, mid, mid]), axis=1)))
+
+    rho = w.rho.reshape(-1)
+    split = 0.5 * ((c1 + r1) + (c2 - r2))
+    star1 = x[:, 0] < split
+    params = {"n": 1.5, "rho_max": (float(rho[star1].max()), float(rho[~star1].max())), "rho_floor": 1e-10,
+              "cell_a": nearest(c1 - r1), "cell_b": nearest(c1 + r1), "cell_c": nearest(c2 - r2),
+              "x_split": split}
+    return w, params

@@ -1,0 +1,104 @@
+"""SCF initial models (Section IV-C) on the GPU through the C ABI: one step against
+the oracle's step on the same seeded inputs, the whole iteration (FMM solve +
+step, repeated) against the oracle's iteration on the 32^3 binary, a solve of the
+oracle's SCF model in both precisions against the oracle FMM, and convergence of
+the iteration on the 64^3 binary."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import scf_oracle
+from paper_2304_11002_gb300 import binding
+from paper_2304_11002_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STATS = binding.SCF_STATS
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_11002_gb300 import build
+    build.build()
+
+
+def _args(p):
+    return (p["n"], p["rho_max"], p["rho_floor"], p["cell_a"], p["cell_b"], p["cell_c"], p["x_split"])
+
+
+def _close_stats(got, ref, tol):
+    """Statistics agree: omega2, C1, C2, W, T, Pi relative to their own size (T and
+    Pi also to |W|), the change and the virial error absolutely."""
+    scale_w = abs(ref["W"])
+    for i, k in enumerate(STATS):
+        if k in ("max_change", "virial_error"):
+            assert abs(got[i] - ref[k]) <= tol, (k, got[i], ref[k])
+        elif k in ("T", "Pi"):
+            assert abs(got[i] - ref[k]) <= tol * scale_w, (k, got[i], ref[k])
+        else:
+            assert abs(got[i] - ref[k]) <= tol * abs(ref[k]), (k, got[i], ref[k])
+
+
+def test_scf_step_matches_oracle():
+    """Seeded density of the 32^3 binary and a seeded smooth potential (not from any
+    solver), one step on each side."""
+    w, p = W.scf_binary("binary32")
+    x = w.tree.leaf_cell_centres()
+    rng = np.random.default_rng(21)
+    k = rng.normal(size=(4, 3)) * 0.2
+    phi = -40.0 + 0.05 * ((x - 16.5) ** 2).sum(axis=1)
+    for kk in k:
+        phi = phi + 2.0 * np.sin(x @ kk)
+    rho = w.rho.reshape(-1) * (1.0 + 0.01 * rng.normal(size=x.shape[0]))
+    ref_rho, ref = scf_oracle.scf_step(w.tree, rho, phi, *_args(p))
+    fmm = binding.OctoFMM(w.tree)
+    r = torch.from_numpy(rho.copy()).cuda()
+    st = binding.octo_fmm_scf_step(fmm.handle, p, r, torch.from_numpy(phi).cuda())
+    got = r.cpu().numpy()
+    assert np.max(np.abs(got - ref_rho)) <= 1e-12 * max(p["rho_max"])
+    _close_stats(st, ref, 1e-12)
+
+
+def test_scf_iteration_matches_oracle_and_its_model_solves():
+    """Five steps of the iteration on the 32^3 binary, each on the FMM potential of the
+    current density, against the oracle's iteration; then the oracle's SCF model
+    solved on the GPU in both precisions against the oracle FMM."""
+    steps = 5
+    w, p = W.scf_binary("binary32")
+    ref_rho, ref_hist = scf_oracle.scf_solve(w.tree, w.rho, *_args(p), steps)
+    fmm = binding.OctoFMM(w.tree)
+    r = torch.from_numpy(w.rho.reshape(-1).copy()).cuda()
+    hist = binding.octo_fmm_scf_solve(fmm.handle, p, r, steps, 0.0)
+    assert hist.shape == (steps, 8)
+    for i in range(steps):
+        _close_stats(hist[i], ref_hist[i], 1e-9)
+    assert np.max(np.abs(r.cpu().numpy() - ref_rho)) <= 1e-9 * max(p["rho_max"])
+    # the model: a solve in both precisions against the oracle
+    po, go, _ = oracle.fmm(w.tree, ref_rho)
+    rr = torch.from_numpy(ref_rho.copy()).cuda()
+    for precision, tol in ((binding.OCTO_FP64, 1e-12), (binding.OCTO_MIXED, 1e-6)):
+        h = binding.OctoFMM(w.tree, 0.5, precision)
+        phi, g = h.forces(rr)
+        torch.cuda.synchronize()
+        phi, g = phi.cpu().numpy(), g.cpu().numpy()
+        assert np.max(np.abs(phi - po) / np.abs(po)) <= tol
+        assert np.max(np.linalg.norm(g - go, axis=0)) <= tol * np.max(np.linalg.norm(go, axis=0))
+
+
+def test_scf_converges_binary64():
+    """The iteration on the 64^3 binary settles: the largest density change falls
+    below 1e-6 of the maximum density, and the virial error of the converged model is
+    small (its floor is the discretisation of the stars by cells)."""
+    w, p = W.scf_binary("binary64")
+    fmm = binding.OctoFMM(w.tree)
+    r = torch.from_numpy(w.rho.reshape(-1).copy()).cuda()
+    hist = binding.octo_fmm_scf_solve(fmm.handle, p, r, 200, 1e-6)
+    ch = hist[:, 3]
+    print("steps", len(ch), "change", ch[[0, len(ch) // 2, -1]], "virial error", hist[-1, 7], "omega2", hist[-1, 0])
+    assert ch[-1] < 1e-6, ch[-5:]
+    assert hist[-1, 7] < 0.05, hist[-1]
+    rho = r.cpu().numpy()
+    assert np.all(np.isfinite(rho)) and np.all(rho > 0)
