@@ -198,6 +198,9 @@ constexpr int64_t kNearFlopsPer2Pairs = 2 + 4 * 2;
 // 15, (L2 d) 15, L0 21, L1 12, dg 3, plus L2 / L3 updates 22 at refined cells or
 // L2P (g, near field) 7 at leaf cells.
 constexpr int64_t kM2MFlopsPerCell = 8 * (7 + 3 + 3 + 18 + 64) + 3;
+// parent cells whose children are point masses (leaf child node): M2 6 fused
+// multiply-adds, M3 10 multiplies and 10 fused multiply-adds per child
+constexpr int64_t kM2MFlopsPointChildren = 8 * (7 + 3 + 3 + 12 + 30) + 3;
 constexpr int64_t kL2LFlopsInterior = 99 + 22, kL2LFlopsLeaf = 99 + 7;
 // exact point-mass pair: R (3), r^2 (5), reciprocal square root (8), m/r, m/r^3 (3), phi and g (7)
 constexpr int64_t kP2PFlopsPerPair = 26;
@@ -213,10 +216,15 @@ void make_stages(octo_fmm* h) {
     const int64_t f_int = m2l_pair_flops<true, true>(), f_leaf = m2l_pair_flops<false, false>();
     switch (kind) {
       case S_P2M: bytes = cells * 16; break;                      // rho in, m out
-      case S_M2M:                                                  // 8 children in, parent out
-        bytes = cells * (8 * 20 + 20) * 8;
-        near = cells * kM2MFlopsPerCell;
+      case S_M2M: {  // 8 children in, parent out (point-mass children: only m and X read)
+        int64_t point = 0;  // parent cells whose children are point masses
+        for (int k = a; k < b; ++k)
+          if (P.children[8 * k] >= 0)
+            for (int o = 0; o < 8; ++o) point += P.children[8 * P.children[8 * k + o]] < 0 ? kCells / 8 : 0;
+        bytes = (cells - point) * (8 * 20 + 20) * 8 + point * (8 * 4 + 20) * 8;
+        near = (cells - point) * kM2MFlopsPerCell + point * kM2MFlopsPointChildren;
         break;
+      }
       case S_M2L: far = pairs * f_int; break;
       case S_CONV:  // mixed precision: the near field is the separate S_NEAR stage
         far = P.kernel_pairs[1] * kConvFlopsPerPair + P.kernel_pairs[3] * f_leaf;
