@@ -122,6 +122,10 @@ void free_all(octo_fmm* h) {
     if (p) cudaFree(p);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (cudaStream_t io : h->io_stream)
+    if (io) cudaStreamDestroy(io);
+  for (cudaEvent_t ev : h->io_event)
+    if (ev) cudaEventDestroy(ev);
   for (auto& ev : h->ev)
     if (ev) cudaEventDestroy(ev);
 }
@@ -932,15 +936,50 @@ int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host,
   double* d_rho = h->d_io;
   double* d_phi = h->d_io + n;
   double* d_g = h->d_io + 2 * n;
+  constexpr int K = octo_fmm::kIoStreams;
+  static_assert(K == 4, "the results go out as phi and the three components of g, one stream each");
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < K && e == cudaSuccess; ++i)
+    if (!h->io_stream[i]) e = cudaStreamCreateWithFlags(&h->io_stream[i], cudaStreamNonBlocking);
+  for (int i = 0; i <= K && e == cudaSuccess; ++i)
+    if (!h->io_event[i]) e = cudaEventCreateWithFlags(&h->io_event[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(h, e, "host-copy streams");
   // Straight between the caller's (pageable) buffers and the device: on a Grace host
   // the copy engines read and write pageable memory through the coherent link at the
-  // same rate as pinned memory, so a host-side staging copy would only add time.
-  cudaError_t e = cudaMemcpyAsync(d_rho, rho_host, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  // rate of pinned memory, so a host-side staging copy would only add time.  The
+  // copies are split over K streams (rho in K pieces; phi and the three components
+  // of g out) so that several copy engines move them at once; events order them
+  // after the caller's earlier work on `stream` and the solve after them.
+  auto fork = [&]() {  // the K streams wait for everything enqueued on s so far
+    cudaError_t r = cudaEventRecord(h->io_event[K], s);
+    for (int i = 0; i < K && r == cudaSuccess; ++i) r = cudaStreamWaitEvent(h->io_stream[i], h->io_event[K], 0);
+    return r;
+  };
+  auto join = [&]() {  // s waits for everything enqueued on the K streams
+    cudaError_t r = cudaSuccess;
+    for (int i = 0; i < K && r == cudaSuccess; ++i) {
+      r = cudaEventRecord(h->io_event[i], h->io_stream[i]);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(s, h->io_event[i], 0);
+    }
+    return r;
+  };
+  e = fork();
+  const int64_t piece = (n + K - 1) / K;
+  for (int i = 0; i < K && e == cudaSuccess; ++i) {
+    const int64_t b = std::min(n, i * piece), c = std::min(n, (i + 1) * piece);
+    if (c > b)
+      e = cudaMemcpyAsync(d_rho + b, rho_host + b, sizeof(double) * (c - b), cudaMemcpyHostToDevice, h->io_stream[i]);
+  }
+  if (e == cudaSuccess) e = join();
   if (e != cudaSuccess) return cuda_fail(h, e, "copy rho in");
   int rc = octo_fmm_forces(h, d_rho, d_phi, d_g, stream);
   if (rc != OCTO_OK) return rc;
-  e = cudaMemcpyAsync(phi_host, d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(g_host, d_g, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
+  e = fork();
+  double* dst[K] = {phi_host, g_host, g_host + n, g_host + 2 * n};
+  const double* src[K] = {d_phi, d_g, d_g + n, d_g + 2 * n};
+  for (int i = 0; i < K && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(dst[i], src[i], sizeof(double) * n, cudaMemcpyDeviceToHost, h->io_stream[i]);
+  if (e == cudaSuccess) e = join();
   int err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -113,6 +113,11 @@ struct octo_fmm {
 
   // graph
   cudaStream_t cap_stream = nullptr;
+  // host-buffer path: streams whose copies run on separate copy engines at once,
+  // and the events that order them against the caller's stream (created on first use)
+  static constexpr int kIoStreams = 4;
+  cudaStream_t io_stream[kIoStreams] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t io_event[kIoStreams + 1] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaGraphExec_t gexec = nullptr;
   const double* g_rho = nullptr;
   double *g_phi = nullptr, *g_g = nullptr;

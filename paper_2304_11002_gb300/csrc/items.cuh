@@ -562,7 +562,8 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
       const int* offs = reinterpret_cast<const int*>(sbuf + (b & 1) * kLeafTableBlockBytes);
       const float4* ks = reinterpret_cast<const float4*>(offs + kLeafBlock);
       // one stencil entry: the two cells' masses times the entry's kernel row
-      auto entry = [&](int u, int off, float* pa, float* pb) {
+      auto entry = [&](int u, float* pa, float* pb) {
+        const int off = offs[u];
         const float4 k = ks[u];
         const float m0 = halo32[lane_f + off], m1 = halo32[lane_f + off + dz];
         pa[0] = fmaf(m0, k.x, pa[0]);
@@ -576,22 +577,12 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
       };
       float pa[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       const int n_in = min(kLeafBlock, n_far - b * kLeafBlock);
-      if (n_in == kLeafBlock) {
-        // full block fully unrolled (constant offsets, no loop control); the halo
-        // offsets four at a time (one 16-byte shared-memory load per four entries:
-        // the loop is bound by the shared-memory load path)
-        const int4* offs4 = reinterpret_cast<const int4*>(offs);
+      if (n_in == kLeafBlock) {  // full block fully unrolled (constant offsets, no loop control)
 #pragma unroll
-        for (int u = 0; u < kLeafBlock; u += 4) {
-          const int4 o = offs4[u >> 2];
-          entry(u, o.x, pa, pb);
-          entry(u + 1, o.y, pa, pb);
-          entry(u + 2, o.z, pa, pb);
-          entry(u + 3, o.w, pa, pb);
-        }
+        for (int u = 0; u < kLeafBlock; ++u) entry(u, pa, pb);
       } else {
 #pragma unroll 4
-        for (int u = 0; u < n_in; ++u) entry(u, offs[u], pa, pb);
+        for (int u = 0; u < n_in; ++u) entry(u, pa, pb);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) f[0][k].add(pa[k]), f[1][k].add(pb[k]);

@@ -90,8 +90,8 @@ def test_scf_iteration_matches_oracle_and_its_model_solves():
 
 def test_scf_converges_binary64():
     """The iteration on the 64^3 binary settles: the largest density change falls
-    below 1e-5 of the maximum density (measured: 5e-2 at the first step, 6e-6 after
-    about 100 steps, then a slow drift), and the virial error of the model is small
+    below 1e-5 of the maximum density (measured: 5e-2 at the first step, 7.9e-6 at
+    step 25, 6e-6 after about 100 steps), and the virial error of the model is small
     (measured 0.016; its floor is the discretisation of the stars by cells)."""
     w, p = W.scf_binary("binary64")
     fmm = binding.OctoFMM(w.tree)
