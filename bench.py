@@ -159,10 +159,10 @@ def kernel_sources_sha256(read=None):
     return h.hexdigest()
 
 
-def recorded_traffic(stage: str, workload: str, shape=None, blocks=None):
+def recorded_traffic(stage: str, workload: str, shape=None, blocks=None, paced=None):
     """(bytes per launch, source) of a matching capture, or (None, reason).  shape
-    (entries per float32 partial, split) and blocks (register budget) must match the
-    capture's when both are known."""
+    (entries per float32 partial, split), blocks (register budget) and paced (queue)
+    must match the capture's when both are known."""
     try:
         with open(TRAFFIC_FILE) as f:
             entries = json.load(f)["entries"]
@@ -177,6 +177,8 @@ def recorded_traffic(stage: str, workload: str, shape=None, blocks=None):
                 return None, "the capture is of another interior shape"
             if blocks is not None and e.get("blocks_per_sm") is not None and blocks != e["blocks_per_sm"]:
                 return None, "the capture is of another register budget"
+            if paced is not None and e.get("paced") is not None and bool(paced) != bool(e["paced"]):
+                return None, "the capture is of the other queue"
             return int(e["bytes"]), e["command"]
     return None, "no capture for this kernel and workload"
 
@@ -320,7 +322,7 @@ STRATEGY = {"auto": 0, "per-kind": 1, "persistent": 2}
 
 
 def time_solver(w, precision, steps, warmup, torch, flush, stream, strategy="auto", blocks=0, corr64=False,
-                shape=None):
+                shape=None, paced=None):
     from paper_2304_11002_gb300 import binding
     fmm = binding.OctoFMM(w.tree, w.theta, precision)
     h = fmm.handle
@@ -330,6 +332,8 @@ def time_solver(w, precision, steps, warmup, torch, flush, stream, strategy="aut
     if shape and precision == binding.OCTO_MIXED:  # interior shape fixed instead of autotuned
         binding.octo_fmm_set_option(h, 6, shape[0])
         binding.octo_fmm_set_option(h, 7, shape[1])
+    if paced is not None and precision == binding.OCTO_MIXED:  # queue fixed instead of autotuned
+        binding.octo_fmm_set_option(h, 8, paced)
     if strategy != "auto":
         binding.octo_fmm_set_option(h, 3, STRATEGY[strategy])
         if blocks:
@@ -445,7 +449,7 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         fmm, info, step_ms, stage_ms, launches, bufs = time_solver(w, precision, args.steps, args.warmup, torch,
                                                                    flush, stream, args.strategy, args.blocks,
-                                                                   args.corr64, args.interior_shape)
+                                                                   args.corr64, args.interior_shape, args.paced)
     barrier()
     t_step = float(np.mean(step_ms))
 
@@ -462,7 +466,8 @@ def run_ours(args):
     roof = roofline_of(info, mean_stage, _measured_peaks(), alu)
     gopt = lambda k: binding.octo_fmm_get_option(fmm.handle, k)  # noqa: E731
     shape = (gopt(6), gopt(7)) if precision == binding.OCTO_MIXED else None
-    roof["traffic"], roof["traffic_source"] = recorded_traffic(roof["kernel"], w.name, shape, gopt(4))
+    roof["traffic"], roof["traffic_source"] = recorded_traffic(roof["kernel"], w.name, shape, gopt(4),
+                                                               gopt(8) if precision == binding.OCTO_MIXED else None)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     nlc = fmm.n_leaf_cells
@@ -488,10 +493,11 @@ def run_ours(args):
                 "register_budget_blocks_per_sm": gopt(4),
                 "autotune_us": {"per_kind": gopt(10), "persistent_1": gopt(11), "persistent_2": gopt(12),
                                 "persistent_3": gopt(13), "interior_chunk_64": gopt(14),
-                                "interior_quarter_node": gopt(15)}}
+                                "interior_quarter_node": gopt(15), "paced_queue": gopt(16)}}
     if precision == binding.OCTO_MIXED:
         strategy["interior_shape"] = {"entries_per_float32_partial": gopt(6),
                                       "items": {1: "half node", 2: "quarter node"}[gopt(7)]}
+        strategy["paced_queue"] = bool(gopt(8))
 
     if precision == binding.OCTO_MIXED and not args.no_fp64:
         del fmm
@@ -663,6 +669,8 @@ def main():
                     help="configurations of --oracle-timing also timed on one thread")
     ap.add_argument("--backward-only", action="store_true",
                     help="time the float64 adjoint (octo_fmm_backward) alone on the workload")
+    ap.add_argument("--paced", type=int, choices=(0, 1), default=None,
+                    help="mixed precision: fix the persistent queue (1 = paced, 0 = merged) instead of autotuning it")
     ap.add_argument("--corr64", action="store_true",
                     help="mixed precision with the angular-momentum correction in float64 (per-kind launches)")
     ap.add_argument("--nominal-peaks", action="store_true",

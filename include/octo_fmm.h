@@ -169,19 +169,23 @@ int octo_fmm_read_state(octo_fmm_t h, int which, double* host_out);
  *  key 7: mixed precision: interior items of half a node with one thread per target
  *         cell (1, default), or of a quarter node with two threads per target cell,
  *         each over one half of the stencil (2).
- *  Keys 6 and 7 fix the interior shape; otherwise the autotuner chooses it (it
- *  changes the float32 summation order, so results differ at float32 rounding).
+ *  key 8: mixed precision, persistent queue: 1 = paced queue (the float32-bound
+ *         and the float64-bound items in two queues, at most one block per SM
+ *         holding a float64 item at a time), 0 = one merged queue (default).
+ *  Keys 6 and 7 fix the interior shape, key 8 the queue; otherwise the autotuner
+ *  chooses them (the shape changes the float32 summation order, so results differ
+ *  at float32 rounding; the queue changes no result).
  * Setting an option drops the captured graph.  Returns OCTO_EINVAL for an unknown
  * key or value. */
 int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value);
 
-/* Reads an option (keys 1-7 above; key 3 reports the strategy in use after
+/* Reads an option (keys 1-8 above; key 3 reports the strategy in use after
  * autotuning) or an autotuner measurement: keys 10, 11, 12, 13 = mean interaction
  * time in microseconds of per-kind launches and of the persistent launch with the
  * 1, 2 and 3 blocks/SM budgets; 0 when not measured (before autotuning, and key 13
- * in float64 mode); keys 14, 15 = mean interaction time in microseconds of the
- * autotuner's shape candidates (chunk 64, quarter-node items; 0 when not
- * measured).  Sizes of the handle (read-only): key 20 = leaf cells
+ * in float64 mode); keys 14, 15, 16 = mean interaction time in microseconds of the
+ * autotuner's later candidates (chunk 64, quarter-node items, paced queue; 0 when
+ * not measured).  Sizes of the handle (read-only): key 20 = leaf cells
  * (n_leaf*512, the length of rho and phi), 21 = CUDA device the handle was created
  * on, 22 = octree nodes, 23 = precision (OCTO_FP64 or OCTO_MIXED), 24 = algorithmic
  * float64 flops of one octo_fmm_backward over its interaction pairs (each pair

@@ -122,10 +122,6 @@ void free_all(octo_fmm* h) {
     if (p) cudaFree(p);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-  for (cudaStream_t io : h->io_stream)
-    if (io) cudaStreamDestroy(io);
-  for (cudaEvent_t ev : h->io_event)
-    if (ev) cudaEventDestroy(ev);
   for (auto& ev : h->ev)
     if (ev) cudaEventDestroy(ev);
 }
@@ -338,6 +334,7 @@ InteractArgs interact_args(const octo_fmm* h) {
   a.queue = h->d_queue;
   a.n_items = h->n_items;
   a.counter = h->d_counter;
+  a.n32 = h->paced ? h->n32 : -1;
   a.grid = h->n_sm * h->persist_per_sm[h->min_blocks];
   a.min_blocks = h->min_blocks;
   a.xc = h->xc;
@@ -447,7 +444,11 @@ ItemCosts default_costs(const Plan& P) {
 // leaf far field) and the float64-bound items (cross, then near items, kind 2) are
 // merged so that every prefix of the queue holds the same fraction of the work of
 // both, so that the two pipes of every SM stay busy side by side.
-std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c, int split = 1) {
+// Paced mode (n32 != nullptr, mixed precision): the float32-bound items in their
+// order, then the float64-bound ones, instead of the merged order; *n32 receives the
+// number of float32-bound items.
+std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c, int split = 1,
+                                 int* n32 = nullptr) {
   std::vector<int32_t> q32, q64, q;
   std::vector<double> w32, w64;
   auto item = [](int node, int kind, int part) { return (node << 4) | (kind << 2) | part; };
@@ -483,6 +484,11 @@ std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c, 
     for (int ci = 0; ci * kCrossSlicesPerItem < n_slices; ++ci) q32.push_back(item(ci, 3, 0));
     return q32;
   }
+  if (n32) {
+    *n32 = (int)q32.size();
+    q32.insert(q32.end(), q64.begin(), q64.end());
+    return q32;
+  }
   double t32 = 0, t64 = 0, c32 = 0, c64 = 0;
   for (double v : w32) t32 += v;
   for (double v : w64) t64 += v;
@@ -504,7 +510,9 @@ std::vector<int32_t> build_queue(const Plan& P, bool mixed, const ItemCosts& c, 
 // (Re)builds the persistent queue for the handle's item costs and interior split
 // and copies it to the device, synchronising stream s.
 cudaError_t load_queue(octo_fmm* h, cudaStream_t s) {
-  const std::vector<int32_t> q = build_queue(h->plan, h->precision == OCTO_MIXED, h->costs, h->st.interior_split);
+  const bool paced = h->paced && h->precision == OCTO_MIXED;
+  const std::vector<int32_t> q = build_queue(h->plan, h->precision == OCTO_MIXED, h->costs, h->st.interior_split,
+                                             paced ? &h->n32 : nullptr);
   if ((int)q.size() > h->queue_cap) return cudaErrorInvalidValue;
   h->n_items = (int)q.size();
   if (q.empty()) return cudaSuccess;
@@ -608,8 +616,8 @@ int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
     e = rebuild_stages(h);
   }
   // 3. interior shape (mixed precision)
+  float t_best = h->tune_ms[best];
   if (e == cudaSuccess && mixed && !h->corr64 && h->requested_shape == 0 && !h->plan.interior_nodes.empty()) {
-    float t_best = h->tune_ms[best];
     h->st.acc_block = 64;
     e = time_interact(h, ts, t0, t1, &h->tune_shape_ms[0]);
     if (e == cudaSuccess && h->tune_shape_ms[0] < t_best)
@@ -620,10 +628,24 @@ int autotune(octo_fmm* h, const double* rho, cudaStream_t s) {
       h->st.interior_split = 2;
       e = load_queue(h, ts);
       if (e == cudaSuccess) e = time_interact(h, ts, t0, t1, &h->tune_shape_ms[1]);
-      if (e == cudaSuccess && !(h->tune_shape_ms[1] < t_best)) {
+      if (e == cudaSuccess && h->tune_shape_ms[1] < t_best) {
+        t_best = h->tune_shape_ms[1];
+      } else if (e == cudaSuccess) {
         h->st.interior_split = 1;
         e = load_queue(h, ts);
       }
+    }
+    if (e == cudaSuccess) e = rebuild_stages(h);
+  }
+  // 4. mixed precision under the persistent queue, unless option 8 fixed it: the
+  //    paced queue (at most one float64 item per SM at a time) against the merged one
+  if (e == cudaSuccess && mixed && h->mode == MODE_PERSISTENT && h->requested_paced == 0) {
+    h->paced = true;
+    e = load_queue(h, ts);
+    if (e == cudaSuccess) e = time_interact(h, ts, t0, t1, &h->tune_shape_ms[2]);
+    if (e == cudaSuccess && !(h->tune_shape_ms[2] < t_best)) {
+      h->paced = false;
+      e = load_queue(h, ts);
     }
     if (e == cudaSuccess) e = rebuild_stages(h);
   }
@@ -823,7 +845,7 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     h->queue_cap = (int)build_queue(P, precision == OCTO_MIXED, h->costs, precision == OCTO_MIXED ? 2 : 1).size();
     e = h->queue_cap > 0 ? dev_malloc(&h->d_queue, sizeof(int32_t) * h->queue_cap) : cudaSuccess;
     if (e == cudaSuccess) e = load_queue(h, h->cap_stream);
-    if (e == cudaSuccess) e = dev_malloc(&h->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc(&h->d_counter, sizeof(int) * (2 + kPaceFlags));
     if (e == cudaSuccess) e = dev_malloc(&h->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
     h->st.err = h->d_err;
@@ -936,50 +958,17 @@ int octo_fmm_forces_host(octo_fmm_t h, const double* rho_host, double* phi_host,
   double* d_rho = h->d_io;
   double* d_phi = h->d_io + n;
   double* d_g = h->d_io + 2 * n;
-  constexpr int K = octo_fmm::kIoStreams;
-  static_assert(K == 4, "the results go out as phi and the three components of g, one stream each");
-  cudaError_t e = cudaSuccess;
-  for (int i = 0; i < K && e == cudaSuccess; ++i)
-    if (!h->io_stream[i]) e = cudaStreamCreateWithFlags(&h->io_stream[i], cudaStreamNonBlocking);
-  for (int i = 0; i <= K && e == cudaSuccess; ++i)
-    if (!h->io_event[i]) e = cudaEventCreateWithFlags(&h->io_event[i], cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_fail(h, e, "host-copy streams");
   // Straight between the caller's (pageable) buffers and the device: on a Grace host
   // the copy engines read and write pageable memory through the coherent link at the
-  // rate of pinned memory, so a host-side staging copy would only add time.  The
-  // copies are split over K streams (rho in K pieces; phi and the three components
-  // of g out) so that several copy engines move them at once; events order them
-  // after the caller's earlier work on `stream` and the solve after them.
-  auto fork = [&]() {  // the K streams wait for everything enqueued on s so far
-    cudaError_t r = cudaEventRecord(h->io_event[K], s);
-    for (int i = 0; i < K && r == cudaSuccess; ++i) r = cudaStreamWaitEvent(h->io_stream[i], h->io_event[K], 0);
-    return r;
-  };
-  auto join = [&]() {  // s waits for everything enqueued on the K streams
-    cudaError_t r = cudaSuccess;
-    for (int i = 0; i < K && r == cudaSuccess; ++i) {
-      r = cudaEventRecord(h->io_event[i], h->io_stream[i]);
-      if (r == cudaSuccess) r = cudaStreamWaitEvent(s, h->io_event[i], 0);
-    }
-    return r;
-  };
-  e = fork();
-  const int64_t piece = (n + K - 1) / K;
-  for (int i = 0; i < K && e == cudaSuccess; ++i) {
-    const int64_t b = std::min(n, i * piece), c = std::min(n, (i + 1) * piece);
-    if (c > b)
-      e = cudaMemcpyAsync(d_rho + b, rho_host + b, sizeof(double) * (c - b), cudaMemcpyHostToDevice, h->io_stream[i]);
-  }
-  if (e == cudaSuccess) e = join();
+  // same rate as pinned memory, so a host-side staging copy would only add time.
+  // (Splitting the copies over several streams gained nothing: a copy to pageable
+  // memory returns only once it is done, so the copies run one after another.)
+  cudaError_t e = cudaMemcpyAsync(d_rho, rho_host, sizeof(double) * n, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "copy rho in");
   int rc = octo_fmm_forces(h, d_rho, d_phi, d_g, stream);
   if (rc != OCTO_OK) return rc;
-  e = fork();
-  double* dst[K] = {phi_host, g_host, g_host + n, g_host + 2 * n};
-  const double* src[K] = {d_phi, d_g, d_g + n, d_g + 2 * n};
-  for (int i = 0; i < K && e == cudaSuccess; ++i)
-    e = cudaMemcpyAsync(dst[i], src[i], sizeof(double) * n, cudaMemcpyDeviceToHost, h->io_stream[i]);
-  if (e == cudaSuccess) e = join();
+  e = cudaMemcpyAsync(phi_host, d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g_host, d_g, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s);
   int err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1095,6 +1084,13 @@ int octo_fmm_set_option(octo_fmm_t h, int key, int64_t value) {
     cudaError_t e = rebuild_stages(h);
     return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "set chunk length");
   }
+  if (key == 8 && (value == 0 || value == 1) && h->precision == OCTO_MIXED) {
+    h->paced = value != 0;
+    h->requested_paced = 1;
+    cudaError_t e = load_queue(h, h->cap_stream);
+    if (e == cudaSuccess) e = rebuild_stages(h);
+    return e == cudaSuccess ? OCTO_OK : cuda_fail(h, e, "set paced queue");
+  }
   if (key == 7 && (value == 1 || (value == 2 && h->precision == OCTO_MIXED && !h->corr64))) {
     h->st.interior_split = (int)value;
     h->requested_shape = 1;
@@ -1164,8 +1160,10 @@ int octo_fmm_get_option(octo_fmm_t h, int key, int64_t* value) {
     case 5: *value = h->corr64 ? 1 : 0; return OCTO_OK;
     case 6: *value = h->st.acc_block; return OCTO_OK;
     case 7: *value = h->st.interior_split; return OCTO_OK;
+    case 8: *value = h->paced ? 1 : 0; return OCTO_OK;
     case 14:
-    case 15: *value = (int64_t)(1000.0f * h->tune_shape_ms[key - 14]); return OCTO_OK;
+    case 15:
+    case 16: *value = (int64_t)(1000.0f * h->tune_shape_ms[key - 14]); return OCTO_OK;
     case 10:
     case 11:
     case 12:

@@ -58,12 +58,15 @@ struct octo_fmm {
   // batched interaction phase: strategy (MODE_*), persistent work queue and counter
   int mode = 0, requested_mode = 0;
   bool corr64 = false;  // mixed precision: correction terms in float64 (option 5)
+  int requested_paced = 0;  // 1: option 8 fixed the paced queue
   int requested_shape = 0;  // 0: the autotuner picks the interior shape; 1: set by options 6 / 7
-  float tune_shape_ms[2] = {0, 0};  // autotune: chunk 64, quarter-node split
+  float tune_shape_ms[3] = {0, 0, 0};  // autotune: chunk 64, quarter-node split, paced queue
   int min_blocks = 1, n_sm = 0;
   int persist_per_sm[4] = {0, 0, 0, 0};  // resident blocks per SM of the persistent variants (index = budget)
   int* d_queue = nullptr;  // sized for the largest queue (interior split 2)
   int n_items = 0, queue_cap = 0;
+  bool paced = false;  // mixed precision: two queues, at most one float64 item per SM (option 8)
+  int n32 = 0;         // paced queue: number of float32-bound items (they come first)
   ItemCosts costs{};  // item costs the queue is ordered by (estimates, then the autotuner's)
   int* d_counter = nullptr;
   int* d_err = nullptr;  // device-side check word of the adjoint kernels
@@ -113,11 +116,6 @@ struct octo_fmm {
 
   // graph
   cudaStream_t cap_stream = nullptr;
-  // host-buffer path: streams whose copies run on separate copy engines at once,
-  // and the events that order them against the caller's stream (created on first use)
-  static constexpr int kIoStreams = 4;
-  cudaStream_t io_stream[kIoStreams] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t io_event[kIoStreams + 1] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaGraphExec_t gexec = nullptr;
   const double* g_rho = nullptr;
   double *g_phi = nullptr, *g_g = nullptr;

@@ -34,20 +34,71 @@ __global__ void __launch_bounds__(items::kThreads, MIXED && !C64 ? 3 : 1)
 // slices of the tabulated cross-level pairs starting at slice node *
 // kCrossSlicesPerItem (sums per slot into xcf; k_cross_apply adds them to the
 // targets after the launch, so that no item writes what another one reads)
+//
+// Paced mode (n32 >= 0, mixed precision): the queue holds the float32-bound items
+// (interior, leaf far field) in [0, n32) and the float64-bound ones (cross, near)
+// in [n32, n_items), each claimed from its own counter (counter[0], counter[1]);
+// counter[2 + smid] flags an SM on which a block holds a float64 item.  A block
+// takes a float64 item only if it can set its SM's flag (so at most one of an
+// SM's blocks keeps the float64 pipe busy while the others run float32 items),
+// and float32 items otherwise; once the float32 items are gone it takes the
+// remaining float64 items regardless.  Nothing waits: a block that cannot set the
+// flag takes other work.  Otherwise (n32 < 0) one counter over the merged queue.
 template <bool MIXED, int MINB, int BLK, int SPLIT>
 __global__ void __launch_bounds__(items::kThreads, MINB)
-    k_persistent(DevTree t, const int* __restrict__ queue, int n_items, int* __restrict__ counter, Stencils st,
-                 const double* __restrict__ mp, const float* __restrict__ mp32, double* __restrict__ loc,
+    k_persistent(DevTree t, const int* __restrict__ queue, int n_items, int n32, int* __restrict__ counter,
+                 Stencils st, const double* __restrict__ mp, const float* __restrict__ mp32, double* __restrict__ loc,
                  double* __restrict__ nearf, int64_t NL, CrossCells xc, double* __restrict__ xcf) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next;
+  bool holding = false, done32 = false, done64 = false;  // thread 0's state in paced mode
+  unsigned smid = 0;
+  if (n32 >= 0) asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  int* flag = counter + 2 + (smid < kPaceFlags ? smid : 0);
+  const bool pace = n32 >= 0 && smid < kPaceFlags;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    if (threadIdx.x == 0) {
+      if (n32 < 0) {
+        const int k = atomicAdd(counter, 1);
+        next = k < n_items ? queue[k] : -1;
+      } else {
+        const int n64 = n_items - n32;
+        if (holding) {
+          atomicExch(flag, 0);
+          holding = false;
+        }
+        int item = -1;
+        if (pace && !done64 && atomicCAS(flag, 0, 1) == 0) {
+          const int k = atomicAdd(counter + 1, 1);
+          if (k < n64) {
+            item = queue[n32 + k];
+            holding = true;
+          } else {
+            atomicExch(flag, 0);
+            done64 = true;
+          }
+        }
+        if (item < 0 && !done32) {
+          const int k = atomicAdd(counter, 1);
+          if (k < n32)
+            item = queue[k];
+          else
+            done32 = true;
+        }
+        if (item < 0 && !done64) {  // no float32 item left: the float64 items regardless
+          const int k = atomicAdd(counter + 1, 1);
+          if (k < n64)
+            item = queue[n32 + k];
+          else
+            done64 = true;
+        }
+        next = item;
+      }
+    }
     __syncthreads();
-    const int k = next;
-    if (k >= n_items) return;
-    const int it = queue[k];
+    const int it = next;
+    if (it < 0) return;
     const int node = it >> 4, part = it & 3, kind = (it >> 2) & 3;
     if (kind == 3) {
       double2* tab2 = reinterpret_cast<double2*>(smem);
@@ -98,10 +149,11 @@ cudaError_t persistent_occupancy(const Stencils& st, const CrossCells& xc, int* 
 template <bool MIXED, int MINB, int BLK, int SPLIT>
 cudaError_t persistent_launch(const DevTree& t, const InteractArgs& a, cudaStream_t s) {
   const size_t smem = persistent_smem_bytes(a.st, a.xc, MIXED);
-  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
+  const int n32 = MIXED ? a.n32 : -1;
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int) * (n32 >= 0 ? 2 + kPaceFlags : 1), s);
   if (e != cudaSuccess) return e;
   k_persistent<MIXED, MINB, BLK, SPLIT><<<a.grid, items::kThreads, smem, s>>>(
-      t, a.queue, a.n_items, a.counter, a.st, a.mp, a.mp32, a.loc, a.nearf, a.NL, a.xc, a.xcf);
+      t, a.queue, a.n_items, n32, a.counter, a.st, a.mp, a.mp32, a.loc, a.nearf, a.NL, a.xc, a.xcf);
   return cudaGetLastError();
 }
 

@@ -76,6 +76,9 @@ struct CrossCells {
   int n_rows;
   int* counter;              // device scratch: next slice to claim (reset by the launcher)
 };
+// SM ids covered by the per-SM flags of the persistent kernel's paced mode (larger
+// ids are not paced); the work counters are 2 + kPaceFlags ints.
+constexpr int kPaceFlags = 1024;
 // Slices of one cross item of the persistent interaction kernel (kind 3).
 constexpr int kCrossSlicesPerItem = 64;
 
@@ -106,7 +109,8 @@ struct InteractArgs {
   int64_t NL;          // leaf cells
   const int* queue;    // persistent queue: (node << 4) | (kind << 2) | part, see kernels_interact.cu
   int n_items;
-  int* counter;        // work counter of the persistent launch (device scratch)
+  int* counter;        // work counters of the persistent launch (device scratch, 2 + 1024 ints)
+  int n32 = -1;        // paced mode: float32-bound items first in the queue (see interact.cuh), else -1
   int grid;            // blocks of the persistent launch (SMs x resident blocks per SM)
   int min_blocks;      // launch-bounds variant of the persistent kernel (1, 2 or 3)
   CrossCells xc;       // tabulated cross-level pairs: cross items of the persistent queue

@@ -198,8 +198,8 @@ def test_errors_are_reported():
 
 @pytest.mark.parametrize("precision", [binding.OCTO_FP64, binding.OCTO_MIXED])
 def test_interaction_strategies_bit_identical(precision):
-    """Per-kind launches and the persistent work queue (every register budget) run
-    the same item functions: identical results for every interior shape (mixed
+    """Per-kind launches and the persistent work queue (every register budget, merged
+    or paced) run the same item functions: identical results for every interior shape (mixed
     precision: 32 or 64 stencil entries per float32 partial sum, half- or
     quarter-node items), each shape within the mixed tolerance of the oracle, and
     the autotuner picks one of the candidates."""
@@ -211,15 +211,19 @@ def test_interaction_strategies_bit_identical(precision):
     po, go, _ = oracle.fmm(w.tree, w.rho) if mixed else (None, None, None)
     cross = None
     first = None
+    # schedules: per-kind launches, the merged persistent queue under every register
+    # budget and (mixed precision) the paced persistent queue
+    schedules = [(1, 1, 0)] + [(2, b, 0) for b in budgets] + ([(2, 3, 1), (2, 1, 1)] if mixed else [])
     for shape in shapes:
         outs = []
-        for mode, minb in [(1, 1)] + [(2, b) for b in budgets]:
+        for mode, minb, paced in schedules:
             fmm = binding.OctoFMM(w.tree, 0.5, precision)
             binding.octo_fmm_set_option(fmm.handle, 3, mode)
             binding.octo_fmm_set_option(fmm.handle, 4, minb)
             if shape is not None:
                 binding.octo_fmm_set_option(fmm.handle, 6, shape[0])
                 binding.octo_fmm_set_option(fmm.handle, 7, shape[1])
+                binding.octo_fmm_set_option(fmm.handle, 8, paced)
             phi, g = fmm.forces(r)
             outs.append((phi.clone(), g.clone()))
             names = _stage_names(fmm)
@@ -248,4 +252,6 @@ def test_interaction_strategies_bit_identical(precision):
         shape = (binding.octo_fmm_get_option(fmm.handle, 6), binding.octo_fmm_get_option(fmm.handle, 7))
         assert shape in shapes
         assert binding.octo_fmm_get_option(fmm.handle, 14) > 0 and binding.octo_fmm_get_option(fmm.handle, 15) > 0
+        if binding.octo_fmm_get_option(fmm.handle, 3) == 2:  # the paced queue was timed
+            assert binding.octo_fmm_get_option(fmm.handle, 16) > 0
         assert _rel_phi(phi.cpu().numpy(), po) <= 1e-6 and _rel_g(g.cpu().numpy(), go) <= 1e-6
