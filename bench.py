@@ -133,7 +133,7 @@ def dist_env():
 # blank lines), else null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 KERNEL_SOURCES = ("capi.cu", "cross.cuh", "device.cuh", "interact.cuh", "items.cuh", "kernels.h",
-                  "kernels_boundary.cu", "kernels_interact.cu", "kernels_interact_b64.cu", "tma.cuh")
+                  "kernels_boundary.cu", "kernels_interact.cu", "kernels_interact_b64.cu", "pair_x2.cuh", "tma.cuh")
 
 
 def code_lines(text: str):

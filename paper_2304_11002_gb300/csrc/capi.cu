@@ -114,7 +114,8 @@ void free_all(octo_fmm* h) {
                   h->d_bnd_index, h->d_mpb,    h->d_locb,
                   h->d_general,  h->d_queue,   h->d_counter, h->d_err,
                   h->d_leaf_far, h->d_leaf_root, h->d_leaf_near,
-                  h->d_leaf_blocks, h->d_scf,  h->d_scf_nodes};
+                  h->d_leaf_blocks, h->d_scf,  h->d_scf_nodes, h->d_st_pair, h->d_st_pair_root,
+                  h->d_cell_pair, h->d_cell_pair_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int64_t* p : {h->xg.d_ft, h->xg.d_fs, h->xg.d_fm, h->xg.d_fsrc, h->xg.d_lt, h->xg.d_ls, h->xg.d_lm,
@@ -736,6 +737,17 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
   up(&h->d_st_parity, P.st_parity);
   up(&h->d_st_root, P.st_root);
   up(&h->d_st_near, P.st_near);
+  std::vector<int32_t> st_pair, st_pair_root;
+  const int n_pair = build_pair_tables(P.st_parity.data(), P.n_st, true, st_pair);
+  const int n_pair_root = build_pair_tables(P.st_root.data(), (int)P.st_root.size(), false, st_pair_root);
+  if (precision == OCTO_MIXED) {
+    std::vector<int32_t> cell_pair, cell_pair_off;
+    build_cell_pair_lists(P.cell_ent, P.cell_ent_off, cell_pair, cell_pair_off);
+    up(&h->d_st_pair, st_pair);
+    up(&h->d_st_pair_root, st_pair_root);
+    up(&h->d_cell_pair, cell_pair);
+    up(&h->d_cell_pair_off, cell_pair_off);
+  }
   int R = 7;
   for (int32_t v : P.st_parity)
     for (int k = 0; k < 3; ++k) R = std::max(R, std::abs((int)(int8_t)((v >> (8 * k)) & 0xff)));
@@ -824,10 +836,11 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
       return create_fail(e == cudaErrorMemoryAllocation ? OCTO_ENOMEM : OCTO_ECUDA, m);
     }
   }
-  h->st = Stencils{h->d_st_parity, P.n_st,       h->d_st_root,   (int)P.st_root.size(), h->d_st_near,
+  h->st = Stencils{h->d_st_parity, P.n_st,       h->d_st_root,   (int)P.st_root.size(), h->d_st_pair, n_pair,
+                   h->d_st_pair_root, n_pair_root, h->d_st_near,
                    (int)P.st_near.size(), h->d_kappa, h->d_leaf_blocks, far_blocks, root_blocks, R, RN,
-                   h->d_cell_ent, h->d_cell_ent_off, h->d_bnd_perm, h->d_bnd_index, h->d_leaf_far, h->d_leaf_root,
-                   h->d_leaf_near, h->d_err};
+                   h->d_cell_ent, h->d_cell_ent_off, h->d_cell_pair, h->d_cell_pair_off, h->d_bnd_perm,
+                   h->d_bnd_index, h->d_leaf_far, h->d_leaf_root, h->d_leaf_near, h->d_err};
   h->xc = CrossCells{h->d_xc_t, h->d_xc_off, h->d_xc_ent, h->d_xc_tab, (int)(P.xc_slice_off.size() - 1),
                      (int)(P.xc_table.size() / 4), h->d_xc_counter};
   e = launch_init_leaf(t, h->d_leaf, (int)P.leaf_nodes.size(), h->d_mp, h->d_mp32, h->cap_stream);

@@ -39,25 +39,36 @@ struct DevTree {
 
 // Float32 copy of the multipoles used by the mixed-precision far field, in units of
 // the cell width h of the cell's level (so that float32 neither overflows nor
-// underflows whatever the physical units): per cell the 20 values
+// underflows whatever the physical units): per cell the 20 values f = 0 .. 19
 //   m, x = (X - c_node) / h (c_node = geometric centre of the node), Q / h^2, O / h^3
-// (same field order as mp), as five float4 planes per node:
-//   mp32 float4 [n_nodes][5][512]   plane k holds values 4k .. 4k + 3,
-// with the 512 cells of a node in parity-major order (mp32_slot): the 64 cells of
-// one parity class (a & 1, b & 1, c & 1) are contiguous, a >> 1 fastest.  The
-// lanes of a parity-class warp hold consecutive (a >> 1, b >> 1, c >> 1), so at any
-// stencil offset they read runs of consecutive 16-byte words of each plane, and
-// the five planes of a source are one address plus constant offsets.
+// (same field order as mp).  The two cells of an x-pair, (2X, b, c) and
+// (2X + 1, b, c), share one record of ten float4 planes,
+//   plane k = (f_2k(2X), f_2k(2X + 1), f_2k+1(2X), f_2k+1(2X + 1)),
+//   mp32 float4 [n_nodes][10][256],
+// so that one 16-byte load returns the same field of both cells as an aligned pair
+// of registers: the operand layout of the paired float32 instructions with which
+// the interior M2L takes two sources at once.  The 256 pair records of a node are in
+// (b & 1, c & 1)-parity-major order (mp32_pair_slot), X fastest: the lanes of a
+// parity-class warp hold consecutive (a >> 1, b >> 1, c >> 1), so at any stencil
+// offset they read runs of consecutive 16-byte words of each plane, and the ten
+// planes of a pair are one address plus constant offsets.
 // Node centres of same-level neighbours differ by exactly 8 h per axis.
-constexpr int kMp32Planes = 5;
+constexpr int kMp32Planes = 10;
+constexpr int kMp32Pairs = 256;
 
-__host__ __device__ __forceinline__ int mp32_slot(int a, int b, int c) {
-  return ((a & 1) + 2 * (b & 1) + 4 * (c & 1)) * 64 + (a >> 1) + 4 * (b >> 1) + 16 * (c >> 1);
+__host__ __device__ __forceinline__ int mp32_pair_slot(int X, int b, int c) {
+  return ((b & 1) + 2 * (c & 1)) * 64 + X + 4 * (b >> 1) + 16 * (c >> 1);
 }
 
-// Plane 0 of local cell (a, b, c), 0 <= a, b, c < 8, of node `node`, as a float4 index.
-__host__ __device__ __forceinline__ int64_t mp32_base(int node, int a, int b, int c) {
-  return (int64_t)node * (kMp32Planes * 512) + mp32_slot(a, b, c);
+// Plane 0 of the record of cells (2X, b, c) and (2X + 1, b, c), 0 <= X < 4,
+// 0 <= b, c < 8, of node `node`, as a float4 index.
+__host__ __device__ __forceinline__ int64_t mp32_pair_base(int node, int X, int b, int c) {
+  return (int64_t)node * (kMp32Planes * kMp32Pairs) + mp32_pair_slot(X, b, c);
+}
+
+// Float index of field f of local cell (a, b, c) of `node`.
+__host__ __device__ __forceinline__ int64_t mp32_index(int node, int a, int b, int c, int f) {
+  return 4 * (mp32_pair_base(node, a >> 1, b, c) + (int64_t)(f >> 1) * kMp32Pairs) + 2 * (f & 1) + (a & 1);
 }
 
 // Compensated float32 sum (Kahan): s holds the running sum, c the negative of the

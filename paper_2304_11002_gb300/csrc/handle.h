@@ -46,6 +46,8 @@ struct octo_fmm {
       *d_leaf_id = nullptr, *d_ijk = nullptr;
   int *d_interior = nullptr, *d_leaf = nullptr, *d_boundary = nullptr;
   int *d_st_parity = nullptr, *d_st_root = nullptr, *d_st_near = nullptr;
+  int *d_st_pair = nullptr, *d_st_pair_root = nullptr;  // x-pair stencils of the mixed interior items
+  int *d_cell_pair = nullptr, *d_cell_pair_off = nullptr;  // x-pair lists of the mixed boundary pairs
   Kappa* d_kappa = nullptr;
   // cross-level pairs: tabulated point-mass pairs and the general remainder (both
   // directions of every pair, so the adjoint gathers over the same lists)

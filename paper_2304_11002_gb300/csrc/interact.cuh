@@ -14,16 +14,21 @@
 namespace octo {
 namespace {
 
-// C64 (mixed precision only): the float64-correction variant of the items.
+// C64 (mixed precision only): the float64-correction variant of the items.  The
+// paired float32 items hold two source records (40 registers) and fit 128
+// registers, two blocks per SM, without spilling.
 template <bool MIXED, bool C64, int BLK, int SPLIT>
-__global__ void __launch_bounds__(items::kThreads, MIXED && !C64 ? 3 : 1)
+__global__ void __launch_bounds__(items::kThreads, MIXED && !C64 ? 2 : 1)
     k_interior_items(DevTree t, const int* __restrict__ nodes, Stencils st, const double* __restrict__ mp,
                      const float* __restrict__ mp32, double* __restrict__ loc) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int parts = MIXED ? 2 * SPLIT : 2;  // items per node
   const int node = nodes[blockIdx.x / parts];
   if constexpr (MIXED)
-    items::interior_f32<C64, BLK, SPLIT>(t, node, blockIdx.x % parts, st, mp32, loc, smem, mp);
+    if constexpr (C64)
+      items::interior_f32<true, BLK, SPLIT>(t, node, blockIdx.x % parts, st, mp32, loc, smem, mp);
+    else
+      items::interior_f32x2<BLK, SPLIT>(t, node, blockIdx.x % parts, st, mp32, loc, smem);
   else
     items::interior_f64(t, node, blockIdx.x & 1, st, mp, loc);
 }
@@ -119,7 +124,7 @@ __global__ void __launch_bounds__(items::kThreads, MINB)
       items::leaf_item<MIXED>(t, node, st, mp, mp32, loc, smem);
     } else {
       if constexpr (MIXED)
-        items::interior_f32<false, BLK, SPLIT>(t, node, SPLIT == 2 ? part : (part & 1), st, mp32, loc, smem, mp);
+        items::interior_f32x2<BLK, SPLIT>(t, node, SPLIT == 2 ? part : (part & 1), st, mp32, loc, smem);
       else
         items::interior_f64(t, node, part & 1, st, mp, loc);
     }

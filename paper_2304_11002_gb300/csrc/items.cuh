@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "pair_x2.cuh"
 #include "tma.cuh"
 
 namespace octo {
@@ -122,15 +123,57 @@ __device__ __forceinline__ void flush_partial(Acc<float>& a, float2* __restrict_
   acc_zero(a);
 }
 
-// One float32 source record (five planes, see device.cuh); base = mp32_base(...).
-__device__ __forceinline__ void load_mp32(const float* __restrict__ mp32, int64_t base, float& m, float x[3],
-                                          float Q[6], float O[10]) {
+// The float32 record of one cell (a, b, c) of `node` (see device.cuh), field by field.
+__device__ __forceinline__ void load_mp32_cell(const float* __restrict__ mp32, int node, int a, int b, int c,
+                                               float& m, float x[3], float Q[6], float O[10]) {
+  const float* r = mp32 + mp32_index(node, a, b, c, 0);
+  auto f = [&](int k) { return __ldg(r + 4 * kMp32Pairs * (k >> 1) + 2 * (k & 1)); };
+  m = f(F_M);
+  for (int i = 0; i < 3; ++i) x[i] = f(F_X + i);
+  for (int i = 0; i < 6; ++i) Q[i] = f(F_Q + i);
+  for (int i = 0; i < 10; ++i) O[i] = f(F_O + i);
+}
+
+// The float32 records of the x-pair of cells at float4 index base (mp32_pair_base):
+// ten 16-byte loads, every field as an F2 (lane 0: cell 2X, lane 1: cell 2X + 1).
+__device__ __forceinline__ void load_mp32_pair(const float* __restrict__ mp32, int64_t base, F2& m, F2 x[3],
+                                               F2 Q[6], F2 O[10]) {
   const float4* r = reinterpret_cast<const float4*>(mp32) + base;
-  const float4 v0 = __ldg(r), v1 = __ldg(r + 512), v2 = __ldg(r + 1024), v3 = __ldg(r + 1536), v4 = __ldg(r + 2048);
-  m = v0.x, x[0] = v0.y, x[1] = v0.z, x[2] = v0.w;
-  Q[0] = v1.x, Q[1] = v1.y, Q[2] = v1.z, Q[3] = v1.w, Q[4] = v2.x, Q[5] = v2.y;
-  O[0] = v2.z, O[1] = v2.w, O[2] = v3.x, O[3] = v3.y, O[4] = v3.z, O[5] = v3.w;
-  O[6] = v4.x, O[7] = v4.y, O[8] = v4.z, O[9] = v4.w;
+  float4 v[kMp32Planes];
+#pragma unroll
+  for (int k = 0; k < kMp32Planes; ++k) v[k] = __ldg(r + k * kMp32Pairs);
+  F2 f[N_MP];
+#pragma unroll
+  for (int k = 0; k < kMp32Planes; ++k) {
+    f[2 * k] = f2(v[k].x, v[k].y);
+    f[2 * k + 1] = f2(v[k].z, v[k].w);
+  }
+  m = f[F_M];
+  for (int i = 0; i < 3; ++i) x[i] = f[F_X + i];
+  for (int i = 0; i < 6; ++i) Q[i] = f[F_Q + i];
+  for (int i = 0; i < 10; ++i) O[i] = f[F_O + i];
+}
+
+// One x-pair of float32 source records at `base` with the stencil-membership mask
+// of a pair entry applied (a lane not in the stencil gets zero mass and moments),
+// and the separation R = X_A - X_B to target position xA, the pair's node being
+// offset by (ox, oy, oz) nodes from the target's.
+__device__ __forceinline__ void pair_sources(const float* __restrict__ mp32, int64_t base, int mask,
+                                             const float xA[3], int ox, int oy, int oz, F2& m, F2 Q[6],
+                                             F2 O[10], F2& R0, F2& R1, F2& R2, F2& rinv) {
+  F2 x[3];
+  load_mp32_pair(mp32, base, m, x, Q, O);
+  if (mask != 3) {
+    const F2 w = f2(mask & 1 ? 1.0f : 0.0f, mask & 2 ? 1.0f : 0.0f);
+    m = m * w;
+    for (int i = 0; i < 6; ++i) Q[i] = Q[i] * w;
+    for (int i = 0; i < 10; ++i) O[i] = O[i] * w;
+  }
+  const float c0 = xA[0] - 8.0f * (float)ox, c1 = xA[1] - 8.0f * (float)oy, c2 = xA[2] - 8.0f * (float)oz;
+  R0 = f2(c0 - x[0].v.x, c0 - x[0].v.y);
+  R1 = f2(c1 - x[1].v.x, c1 - x[1].v.y);
+  R2 = f2(c2 - x[2].v.x, c2 - x[2].v.y);
+  rinv = rsqrt2(fma2(R0, R0, fma2(R1, R1, R2 * R2)));
 }
 
 // Target cell and stencil range of a thread of an interior item.  split 1: part =
@@ -188,7 +231,7 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int par
     tOh64[2] = Oh64[2] + Oh64[7] + Oh64[9];
   }
   float mA, xA[3], QA[6], Oh[10], tOh[3];
-  load_mp32(mp32, mp32_base(node, a, b, c), mA, xA, QA, Oh);
+  load_mp32_cell(mp32, node, a, b, c, mA, xA, QA, Oh);
   {
     const float inv_m = 1.0f / mA;
     for (int i = 0; i < 10; ++i) Oh[i] *= inv_m;
@@ -212,7 +255,7 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int par
       const int snode = __ldg(nb + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
       if (snode < 0) continue;
       float m, x[3], Q[6], O[10];
-      load_mp32(mp32, mp32_base(snode, sa & 7, sb & 7, sc & 7), m, x, Q, O);
+      load_mp32_cell(mp32, snode, sa & 7, sb & 7, sc & 7, m, x, Q, O);
       const float R0 = xA[0] - (x[0] + 8.0f * (float)ox);
       const float R1 = xA[1] - (x[1] + 8.0f * (float)oy);
       const float R2 = xA[2] - (x[2] + 8.0f * (float)oz);
@@ -256,6 +299,80 @@ __device__ __forceinline__ void interior_f32(const DevTree& t, int node, int par
   } else {
     for (int i = 0; i < 3; ++i) out(G_DG + i, ih2);
   }
+}
+
+// The mixed path's interior M2L in paired float32 instructions: the stencil of the
+// thread's parity class grouped into aligned x-pairs of source cells (st.pair, see
+// build_pair_tables), each pair one iteration that loads the two cells' records
+// with ten 16-byte loads (the pair layout of mp32) and computes both M2L pairs at
+// once (m2l_pair_x2).  A stencil entry whose x-partner is not in the stencil is a
+// pair with one lane masked to zero mass and moments.  Same targets, partial-sum
+// blocks (BLK stencil entries, BLK / 2 pairs), compensated flush and split as
+// interior_f32.  Contains a block-wide barrier when SPLIT == 2.
+template <int BLK, int SPLIT>
+__device__ __forceinline__ void interior_f32x2(const DevTree& t, int node, int part, const Stencils& st,
+                                               const float* __restrict__ mp32, double* __restrict__ loc,
+                                               unsigned char* smem) {
+  static_assert(BLK % 2 == 0, "pairs per partial sum");
+  const int lvl = t.level[node];
+  const int ntab = lvl == 0 ? st.n_pair_root : st.n_pair;
+  int p, a, b, c, s_begin, s_end;
+  interior_cell(SPLIT, part, threadIdx.x, ntab, p, a, b, c, s_begin, s_end);
+  const int64_t NC = t.NC;
+  const int64_t tgt = (int64_t)node * 512 + a + 8 * b + 64 * c;
+  float mA, xA[3], QA[6], Oh[10], tOh[3];
+  load_mp32_cell(mp32, node, a, b, c, mA, xA, QA, Oh);
+  {
+    const float inv_m = 1.0f / mA;
+    for (int i = 0; i < 10; ++i) Oh[i] *= inv_m;
+    tOh[0] = Oh[0] + Oh[3] + Oh[5];
+    tOh[1] = Oh[1] + Oh[6] + Oh[8];
+    tOh[2] = Oh[2] + Oh[7] + Oh[9];
+  }
+  const int* tab = lvl == 0 ? st.pair_root + p * st.n_pair_root : st.pair + p * st.n_pair;
+  const int* nb = t.nbr + 27 * node;
+  float2* sc = reinterpret_cast<float2*>(smem) + threadIdx.x;
+  for (int f = 0; f < kInteriorFields; ++f) sc[f * kThreads] = make_float2(0.0f, 0.0f);
+  Acc<float> part_sum;
+  acc_zero(part_sum);
+  for (int s0 = s_begin; s0 < s_end; s0 += BLK / 2) {
+    const int s1 = min(s0 + BLK / 2, s_end);
+    for (int s = s0; s < s1; ++s) {
+      const int e = __ldg(tab + s);
+      int dx, dy, dz;
+      unpack(e, dx, dy, dz);
+      const int sa = a + dx, sb = b + dy, sc_ = c + dz;  // sa even: cells sa, sa + 1
+      const int ox = sa >> 3, oy = sb >> 3, oz = sc_ >> 3;
+      const int snode = __ldg(nb + (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
+      if (snode < 0) continue;
+      F2 m, Q[6], O[10], R0, R1, R2, rinv;
+      pair_sources(mp32, mp32_pair_base(snode, (sa & 7) >> 1, sb & 7, sc_ & 7), (e >> 24) & 3, xA, ox, oy, oz, m, Q,
+                   O, R0, R1, R2, rinv);
+      m2l_pair_x2<true>(R0, R1, R2, m, Q, O, Oh, tOh, rinv, part_sum);
+    }
+    flush_partial(part_sum, sc);
+  }
+  if constexpr (SPLIT == 2) {  // the second stencil half's (sum, compensation) pairs join the first's
+    __syncthreads();
+    if (threadIdx.x >= 128) return;
+    for (int f = 0; f < kInteriorFields; ++f) {
+      const float2 o = sc[f * kThreads + 128];
+      two_sum_into(sc[f * kThreads], o.x);
+      sc[f * kThreads].y += o.y;
+    }
+  }
+  // sum + compensation in float64; unit cell width -> physical units: L_n scales
+  // with h^-(n+1), dg with h^-2
+  const double ih = 1.0 / t.h[lvl], ih2 = ih * ih, ih3 = ih2 * ih, ih4 = ih2 * ih2;
+  auto out = [&](int f, double scale) {
+    const float2 v = sc[f * kThreads];
+    loc[f * NC + tgt] = ((double)v.x + (double)v.y) * scale;
+  };
+  out(G_L0, ih);
+  for (int i = 0; i < 3; ++i) out(G_L1 + i, ih2);
+  for (int i = 0; i < 6; ++i) out(G_L2 + i, ih3);
+  for (int i = 0; i < 10; ++i) out(G_L3 + i, ih4);
+  for (int i = 0; i < 3; ++i) out(G_DG + i, ih2);
 }
 
 // ------------------------------------------------------------ leaf item
@@ -342,6 +459,48 @@ __device__ __forceinline__ void leaf_merge(A& acc, LeafAcc<float>& p) {
   }
 }
 
+// boundary_pairs of the mixed path (float32 correction) by x-pairs of source cells:
+// the per-cell lists grouped like the interior stencils (st.cell_pair, see
+// build_cell_pair_lists), two sources per iteration in paired float32 instructions,
+// st.acc_block / 2 pairs per float32 partial sum.
+template <typename A>
+__device__ __forceinline__ void boundary_pairs_x2(const DevTree& t, int node, int l, const Stencils& st,
+                                                  const float* __restrict__ mp32, A& acc) {
+  const int a = l & 7, b = (l >> 3) & 7, c = l >> 6;
+  const int* nb = t.nbr + 27 * node;
+  float xA[3];
+  for (int i = 0; i < 3; ++i) xA[i] = __ldg(mp32 + mp32_index(node, a, b, c, F_X + i));
+  LeafAcc<float> part = {0.0f, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+  int n_part = 0;
+  // the lanes advance through their (slot, pair) lists independently, as in
+  // boundary_pairs
+  int o = -1, e = 0, e1 = 0, sn = -1, ox = 0, oy = 0, oz = 0;
+  for (;;) {
+    while (e == e1 && o < 27) {
+      if (++o == 27) break;
+      sn = nb[o];
+      if (sn < 0 || t.children[8 * sn] < 0) continue;  // refined neighbours only
+      ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+      e = __ldg(st.cell_pair_off + l * 27 + o), e1 = __ldg(st.cell_pair_off + l * 27 + o + 1);
+    }
+    if (o == 27) break;
+    const int en = __ldg(st.cell_pair + e);
+    int dx, dy, dz;
+    unpack(en, dx, dy, dz);
+    const int sa = a + dx, sb = b + dy, sc = c + dz;  // sa even
+    F2 m, Q[6], O[10], R0, R1, R2, rinv;
+    pair_sources(mp32, mp32_pair_base(sn, (sa & 7) >> 1, sb & 7, sc & 7), (en >> 24) & 3, xA, ox, oy, oz, m, Q, O,
+                 R0, R1, R2, rinv);
+    m2l_pair_x2<false>(R0, R1, R2, m, Q, O, nullptr, nullptr, rinv, part);
+    if (++n_part == st.acc_block / 2) {
+      leaf_merge(acc, part);
+      n_part = 0;
+    }
+    ++e;
+  }
+  leaf_merge(acc, part);
+}
+
 // M2L from refined same-level neighbours into leaf cell l of a leaf node (leaf
 // target: L0, L1, dg).  The per-cell entry lists hold only offsets whose source
 // lies in the neighbour slot, so every iteration of every lane is a valid pair.
@@ -351,6 +510,10 @@ template <bool MIXED, typename A, bool C64 = false>
 __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l, const Stencils& st,
                                                const double* __restrict__ mp, const float* __restrict__ mp32,
                                                A& acc, DgAcc* d64 = nullptr) {
+  if constexpr (MIXED && !C64) {
+    boundary_pairs_x2(t, node, l, st, mp32, acc);
+    return;
+  }
   using T = typename std::conditional<MIXED, float, double>::type;
   const int64_t NC = t.NC;
   const int a = l & 7, b = (l >> 3) & 7, c = l >> 6;
@@ -358,8 +521,9 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
   const int* nb = t.nbr + 27 * node;
   T xA0, xA1, xA2;
   if constexpr (MIXED) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(mp32) + mp32_base(node, a, b, c));
-    xA0 = v.y, xA1 = v.z, xA2 = v.w;
+    xA0 = __ldg(mp32 + mp32_index(node, a, b, c, F_X + 0));
+    xA1 = __ldg(mp32 + mp32_index(node, a, b, c, F_X + 1));
+    xA2 = __ldg(mp32 + mp32_index(node, a, b, c, F_X + 2));
   } else {
     xA0 = mp[(F_X + 0) * NC + tgt], xA1 = mp[(F_X + 1) * NC + tgt], xA2 = mp[(F_X + 2) * NC + tgt];
   }
@@ -390,7 +554,7 @@ __device__ __forceinline__ void boundary_pairs(const DevTree& t, int node, int l
       T R0, R1, R2, m, Q[6], O[10], rinv;
       if constexpr (MIXED) {
         float x[3];
-        load_mp32(mp32, mp32_base(sn, sa & 7, sb & 7, sc & 7), m, x, Q, O);
+        load_mp32_cell(mp32, sn, sa & 7, sb & 7, sc & 7, m, x, Q, O);
         R0 = xA0 - (x[0] + 8.0f * (float)ox);
         R1 = xA1 - (x[1] + 8.0f * (float)oy);
         R2 = xA2 - (x[2] + 8.0f * (float)oz);

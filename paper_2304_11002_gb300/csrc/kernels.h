@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "device.cuh"
 
@@ -26,6 +27,13 @@ struct Stencils {
   int n_st;
   const int* root;    // level-0 far offsets
   int n_root;
+  // Mixed path's interior items: the stencils grouped into aligned x-pairs of source
+  // cells per parity class (build_pair_tables): packed offset of the even cell, bit
+  // 24 / 25 set when the even / odd cell is in the stencil.
+  const int* pair;       // [8][n_pair]       parity stencils
+  int n_pair;
+  const int* pair_root;  // [8][n_pair_root]  level-0 stencil
+  int n_pair_root;
   const int* near_;   // non-zero near offsets
   int n_near;
   const Kappa* kappa;    // dense monopole kernel table over [-R, R]^3, unit cell width
@@ -38,6 +46,8 @@ struct Stencils {
   int near_radius;       // maximum |offset component| of the near offsets
   const int* cell_ent;   // parity offsets per (cell, neighbour slot), see Plan::cell_ent
   const int* cell_ent_off;
+  const int* cell_pair;      // mixed path: the lists of cell_ent grouped into x-pairs of
+  const int* cell_pair_off;  // source cells (build_cell_pair_lists), same indexing
   const unsigned short* bnd_perm;  // per boundary leaf node: its 512 cells by decreasing load
   const int* bnd_index;            // per node: row of bnd_perm or -1
   // Leaf items, per parity class p of the target cell and stencil entry s:
@@ -52,6 +62,19 @@ struct Stencils {
                             // 2: an item is a quarter node, two threads per target cell (one
                             //    stencil half each, merged at the end)
 };
+
+// Host: the stencil tab (n packed offsets; per_parity: [8][n], else one table for
+// every parity class) grouped into aligned x-pairs of source cells for each parity
+// class p: the entries dx, dx' with floor((p_x + dx) / 2) = floor((p_x + dx') / 2)
+// and equal dy, dz form one pair, in the order of their first entry.  Returns the
+// pairs per class (every class padded to the largest with entries of no cell).
+int build_pair_tables(const int* tab, int n, bool per_parity, std::vector<int32_t>& out);
+
+// Host: the per-(cell, neighbour slot) offset lists (ent, off: list i spans
+// ent[off[i] .. off[i + 1]), i = l * 27 + o for local cell l) grouped into aligned
+// x-pairs of source cells as in build_pair_tables, for the x-parity of cell l.
+void build_cell_pair_lists(const std::vector<int32_t>& ent, const std::vector<int32_t>& off,
+                           std::vector<int32_t>& pair_ent, std::vector<int32_t>& pair_off);
 
 // Host: the leaf-item tables above for the given stencils and precision mode.
 void build_leaf_tables(const int* parity, int n_st, const int* root, int n_root, const int* near_, int n_near, int R,

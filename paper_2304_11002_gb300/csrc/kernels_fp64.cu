@@ -23,9 +23,11 @@ __global__ void k_init_leaf(DevTree t, const int* __restrict__ nodes, double* __
     mp[(F_X + 2) * NC + cell] = t.origin[2] + h * ((double)(8 * ijk[3 * node + 2] + c) + 0.5);
     for (int f = F_Q; f < N_MP; ++f) mp[f * NC + cell] = 0.0;
     if (mp32) {  // cell centre relative to the node centre, in cell widths (exact)
-      float4* r = reinterpret_cast<float4*>(mp32) + mp32_base(node, a, b, c);
-      r[0] = make_float4(0.0f, (float)a - 3.5f, (float)b - 3.5f, (float)c - 3.5f);
-      for (int k = 1; k < kMp32Planes; ++k) r[512 * k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float* r = mp32 + mp32_index(node, a, b, c, 0);  // field f at r + mp32_index(.., f) - mp32_index(.., 0)
+      for (int f = 0; f < N_MP; ++f) {
+        const float v = f == F_X + 0 ? (float)a - 3.5f : f == F_X + 1 ? (float)b - 3.5f : f == F_X + 2 ? (float)c - 3.5f : 0.0f;
+        r[4 * kMp32Pairs * (f >> 1) + 2 * (f & 1)] = v;
+      }
     }
   }
 }
@@ -44,7 +46,7 @@ __global__ void k_p2m(DevTree t, const int* __restrict__ nodes, const double* __
     const double r = rho[lid * 512 + l];
     const double m = r * h3;
     mp[(int64_t)node * 512 + l] = m;
-    if (mp32) mp32[4 * mp32_base(node, l & 7, (l >> 3) & 7, l >> 6)] = (float)m;
+    if (mp32) mp32[mp32_index(node, l & 7, (l >> 3) & 7, l >> 6, F_M)] = (float)m;
     const bool bad = !(r > 0.0 && isfinite(r));  // NaN, <= 0 or +inf
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrDensity);
   }
@@ -162,15 +164,15 @@ __global__ void __launch_bounds__(kM2MThreads, 12) k_m2m(DevTree t, int node_beg
     const double c0 = t.origin[0] + h * (8.0 * t.ijk[3 * node + 0] + 4.0);
     const double c1 = t.origin[1] + h * (8.0 * t.ijk[3 * node + 1] + 4.0);
     const double c2 = t.origin[2] + h * (8.0 * t.ijk[3 * node + 2] + 4.0);
-    float v[4 * kMp32Planes];
+    float v[N_MP];
     v[F_M] = (float)m;
     v[F_X + 0] = (float)((X0 - c0) * ih);
     v[F_X + 1] = (float)((X1 - c1) * ih);
     v[F_X + 2] = (float)((X2 - c2) * ih);
     for (int i = 0; i < 6; ++i) v[F_Q + i] = (float)(Q[i] * ih2);
     for (int i = 0; i < 10; ++i) v[F_O + i] = (float)(O[i] * ih3);
-    float4* r = reinterpret_cast<float4*>(mp32) + mp32_base(node, a, b, c);
-    for (int k = 0; k < kMp32Planes; ++k) r[512 * k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    float* r = mp32 + mp32_index(node, a, b, c, 0);
+    for (int f = 0; f < N_MP; ++f) r[4 * kMp32Pairs * (f >> 1) + 2 * (f & 1)] = v[f];
   }
 }
 

@@ -15,8 +15,10 @@ namespace octo {
 
 namespace {
 
+// The mixed path's paired boundary pairs fit 128 registers (two blocks per SM)
+// without spilling.
 template <bool MIXED, bool C64 = false>
-__global__ void __launch_bounds__(items::kThreads, MIXED && !C64 ? 3 : 1)
+__global__ void __launch_bounds__(items::kThreads, MIXED && !C64 ? 2 : 1)
     k_leaf_items(DevTree t, const int* __restrict__ nodes, Stencils st, const double* __restrict__ mp,
                  const float* __restrict__ mp32, double* __restrict__ loc) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -46,6 +48,56 @@ void build_leaf_tables(const int* parity, int n_st, const int* root, int n_root,
     for (int s = 0; s < n_st; ++s) far_out[p * n_st + s] = entry(gf, pa, pb, pc, parity[p * n_st + s]);
     for (int s = 0; s < n_root; ++s) root_out[p * n_root + s] = entry(gf, pa, pb, pc, root[s]);
     for (int s = 0; s < n_near; ++s) near_out[p * n_near + s] = entry(gn, pa, pb, pc, near_[s]);
+  }
+}
+
+namespace {
+
+// The entries tp[0 .. n) for targets of x-parity pa grouped into aligned x-pairs of
+// source cells, appended to out in the order of their first entry.
+void group_pairs(const int* tp, int n, int pa, std::vector<int32_t>& out) {
+  std::vector<std::pair<int32_t, size_t>> key_slot;  // (pair index X, dy, dz) -> slot
+  for (int s = 0; s < n; ++s) {
+    const int e = tp[s];
+    const int dx = (int)(int8_t)(e & 0xff), dy = (int)(int8_t)((e >> 8) & 0xff), dz = (int)(int8_t)((e >> 16) & 0xff);
+    const int v = pa + dx, X = v >= 0 ? v / 2 : -((1 - v) / 2), bit = v - 2 * X;  // X = floor(v / 2)
+    const int32_t key = (int32_t)(((uint32_t)(X & 0xff)) | ((uint32_t)(dy & 0xff) << 8) | ((uint32_t)(dz & 0xff) << 16));
+    size_t slot = out.size();
+    for (const auto& ks : key_slot)
+      if (ks.first == key) slot = ks.second;
+    if (slot == out.size()) {
+      key_slot.push_back({key, slot});
+      const int dx0 = 2 * X - pa;  // a + dx0 is even for targets of x-parity pa
+      out.push_back((int32_t)(((uint32_t)(dx0 & 0xff)) | ((uint32_t)(dy & 0xff) << 8) | ((uint32_t)(dz & 0xff) << 16)));
+    }
+    out[slot] |= (int32_t)(1u << (24 + bit));
+  }
+}
+
+}  // namespace
+
+int build_pair_tables(const int* tab, int n, bool per_parity, std::vector<int32_t>& out) {
+  std::vector<std::vector<int32_t>> per(8);
+  size_t n_pair = 0;
+  for (int p = 0; p < 8; ++p) {
+    group_pairs(per_parity ? tab + (size_t)p * n : tab, n, p & 1, per[p]);
+    n_pair = std::max(n_pair, per[p].size());
+  }
+  out.assign(8 * n_pair, 0);
+  for (int p = 0; p < 8; ++p)
+    for (size_t s = 0; s < n_pair; ++s)  // padding: the first pair's offset with no cell
+      out[p * n_pair + s] = s < per[p].size() ? per[p][s] : (per[p][0] & 0xffffff);
+  return (int)n_pair;
+}
+
+void build_cell_pair_lists(const std::vector<int32_t>& ent, const std::vector<int32_t>& off,
+                           std::vector<int32_t>& pair_ent, std::vector<int32_t>& pair_off) {
+  pair_ent.clear();
+  pair_off.assign(1, 0);
+  for (size_t i = 0; i + 1 < off.size(); ++i) {
+    const int l = (int)(i / 27);
+    group_pairs(ent.data() + off[i], off[i + 1] - off[i], (l & 7) & 1, pair_ent);
+    pair_off.push_back((int32_t)pair_ent.size());
   }
 }
 
