@@ -807,26 +807,10 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     if (e == cudaSuccess) e = upload(&h->d_leaf_root, lr);
     if (e == cudaSuccess) e = upload(&h->d_leaf_near, ln);
     if (precision == OCTO_MIXED) {
-      // blocks of 32 entries: 32 int32 halo offsets, then 32 float4 kernel rows
-      // (zero-padded past the end of a stencil); parity stencils, then level 0
-      far_blocks = (ns + kLeafBlock - 1) / kLeafBlock;
-      root_blocks = (nr + kLeafBlock - 1) / kLeafBlock;
-      constexpr int kWords = kLeafTableBlockBytes / 16;
-      std::vector<uint4> blk((size_t)8 * (far_blocks + root_blocks) * kWords, make_uint4(0, 0, 0, 0));
-      size_t b0 = 0;
-      for (auto [tab, n, nb] : {std::tuple{&lf, ns, far_blocks}, {&lr, nr, root_blocks}})
-        for (int p = 0; p < 8; ++p)
-          for (int bk = 0; bk < nb; ++bk, ++b0)
-            for (int u = 0; u < kLeafBlock; ++u) {
-              const int s_ = bk * kLeafBlock + u;
-              if (s_ >= n) break;
-              const int2 en = (*tab)[(size_t)p * n + s_];
-              const Kappa& v = kap[en.y];
-              unsigned char* base = reinterpret_cast<unsigned char*>(&blk[b0 * kWords]);
-              std::memcpy(base + 4 * u, &en.x, 4);
-              const float k4[4] = {(float)v.v[0], (float)v.v[1], (float)v.v[2], (float)v.v[3]};
-              std::memcpy(base + 4 * kLeafBlock + 16 * u, k4, 16);
-            }
+      // z-column blocks (see kLeafBlock): parity stencils, then level 0
+      std::vector<uint4> blk;
+      far_blocks = build_leaf_column_blocks(P.st_parity.data(), ns, true, R, kap.data(), blk);
+      root_blocks = build_leaf_column_blocks(P.st_root.data(), nr, false, R, kap.data(), blk);
       if (e == cudaSuccess) e = upload(&h->d_leaf_blocks, blk);
     }
     if (e != cudaSuccess) {

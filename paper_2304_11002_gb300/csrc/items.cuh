@@ -380,23 +380,26 @@ __device__ __forceinline__ void interior_f32x2(const DevTree& t, int node, int p
 // kept in shared memory split by cell parity: halo coordinate h in [0, 8 + 2r) per
 // axis goes to parity block (hx & 1) + 2 (hy & 1) + 4 (hz & 1), position
 // (hx >> 1, hy >> 1, hz >> 1) in a G^3 sub-grid (G = 4 + r) with row pitch PY and
-// plane pitch PZ.  The 32 lanes of a warp hold one parity class of targets (cells
-// (2i + pa, 2j + pb, 2k + pc), i, j < 4, k < 2), so for any stencil offset their
-// sources are (i + u, j + v, k + w) in one parity block: lane offsets i + PY j + PZ k.
-// Far halo: PY = 12 (mod 32) and PZ = 16 (mod 32) make the 32 float32 loads hit 32
-// distinct banks, and the 16 float64 loads of each half-warp 16 distinct bank
-// pairs.  The near float64 halo of the mixed path is dense (small radius).
+// plane pitch PZ.  The 32 lanes of a warp hold targets of one parity class (cells
+// (2i + pa, 2j + pb, 2k + pc)), so for any stencil offset their sources are
+// (i + u, j + v, k + w) in one parity block: lane offsets i + PY j + PZ k.
+// Far halo, float64 path (lanes i, j < 4, k < 2 of a parity class): PY = 12 and
+// PZ = 16 (mod 32) make the 16 float64 loads of each half-warp hit 16 distinct bank
+// pairs.  Far halo, mixed path (lanes i, j < 4 and the even k = 2 kh, kh < 2, each
+// lane also holding k + 1): PY = 12 and PZ = 8 (mod 32) make the 32 float32 loads
+// hit 32 distinct banks (i + 12 j + 16 kh).  The near float64 halo of the mixed path
+// is dense (small radius).
 struct HaloGeom {
   int r, G, PY, PZ, PQ;  // border, sub-grid extent, row pitch, plane pitch, parity block size
 };
 
-__host__ __device__ inline HaloGeom far_geom(int r) {
+__host__ __device__ inline HaloGeom far_geom(int r, bool mixed) {
   HaloGeom g;
   g.r = r;
   g.G = 4 + r;
   g.PY = 12;
   while (g.PY < g.G) g.PY += 32;
-  g.PZ = 16;
+  g.PZ = mixed ? 8 : 16;
   while (g.PZ < g.G * g.PY) g.PZ += 32;
   g.PQ = g.G * g.PZ;
   return g;
@@ -423,7 +426,7 @@ __host__ __device__ inline int halo_index(const HaloGeom& g, int hx, int hy, int
 // (kLeafTableBlockBytes each) and their two mbarriers.  The near item of the mixed
 // path needs the near float64 halo.
 __host__ __device__ inline size_t leaf_halo_bytes(const Stencils& st, bool mixed) {
-  const HaloGeom gf = far_geom(st.radius);
+  const HaloGeom gf = far_geom(st.radius, mixed);
   const size_t halo = (mixed ? sizeof(float) : sizeof(double)) * 8 * (size_t)gf.PQ;
   const size_t b = halo > sizeof(double) * 512 * 7 ? halo : sizeof(double) * 512 * 7;
   return (b + 127) & ~(size_t)127;
@@ -627,6 +630,44 @@ __device__ __forceinline__ void stage_halo(const HaloGeom& g, const int* nleaf, 
   }
 }
 
+// stage_halo of the mixed path, from the float32 masses of mp32 (the float32
+// rounding of mp's masses, the same values): each lane loads the two masses of an
+// x-pair of cells (8 bytes) for one halo row, the two halves of a warp take two
+// rows, and each lane keeps kRowPairs loads in flight, so that a block stages its
+// halo in a few round trips to L2.
+__device__ __forceinline__ void stage_halo_mixed(const HaloGeom& g, const int* nleaf, const float* __restrict__ mp32,
+                                                 float* halo) {
+  constexpr int kRowPairs = 6;
+  const int R = g.r, H = 2 * g.G, n_rows = H * H;
+  const int x_first = (-R) & ~1;               // even x of the first pair (floor)
+  const int n_pairs = (7 + R - x_first) / 2 + 1;  // pairs covering x in [-R, 7 + R]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  const int q = lane & 15, sub = lane >> 4;
+  const int x = x_first + 2 * q;
+  for (int r0 = 2 * warp + sub; r0 < n_rows; r0 += 2 * n_warps * kRowPairs) {
+    float2 m[kRowPairs];
+#pragma unroll
+    for (int u = 0; u < kRowPairs; ++u) {
+      const int r = r0 + u * 2 * n_warps;
+      m[u] = make_float2(0.0f, 0.0f);
+      if (r < n_rows && q < n_pairs) {
+        const int y = r % H - R, z = r / H - R;
+        const int sn = nleaf[((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1)];
+        if (sn >= 0) m[u] = __ldg(reinterpret_cast<const float2*>(mp32 + mp32_index(sn, x & 7, y & 7, z & 7, F_M)));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRowPairs; ++u) {
+      const int r = r0 + u * 2 * n_warps;
+      if (r < n_rows && q < n_pairs) {
+        const int hx = x + R, hy = r % H, hz = r / H;
+        if (hx >= 0) halo[halo_index(g, hx, hy, hz)] = m[u].x;
+        if (hx + 1 < H) halo[halo_index(g, hx + 1, hy, hz)] = m[u].y;
+      }
+    }
+  }
+}
+
 // Leaf neighbour table of `node` into shared memory; returns whether any same-level
 // neighbour is refined (block-uniform).  Ends with a barrier.
 __device__ __forceinline__ bool load_leaf_neighbours(const DevTree& t, int node, int* nleaf) {
@@ -641,14 +682,15 @@ __device__ __forceinline__ bool load_leaf_neighbours(const DevTree& t, int node,
 }
 
 // Local index of the q-th (q = 0, 1) cell owned by thread tid in a leaf item.
-// Mixed path: warp w holds parity class w, lane (i, j, k0) the cells
-// (2i + pa, 2j + pb, 2 (k0 + 2q) + pc).  Float64 path: cell_of(q, tid).
+// Mixed path: warp w holds parity class w, lane (i, j, kh) the cells
+// (2i + pa, 2j + pb, 2 (2 kh + q) + pc), adjacent planes of the parity class.
+// Float64 path: cell_of(q, tid).
 template <bool MIXED>
 __host__ __device__ __forceinline__ int leaf_cell(int q, int tid) {
   if (MIXED) {
     const int p = tid >> 5, lane = tid & 31;
     const int a = 2 * (lane & 3) + (p & 1), b = 2 * ((lane >> 2) & 3) + ((p >> 1) & 1);
-    const int c = 2 * ((lane >> 4) + 2 * q) + (p >> 2);
+    const int c = 2 * (2 * (lane >> 4) + q) + (p >> 2);
     return a + 8 * b + 64 * c;
   }
   int p, zh, a, b, c;
@@ -664,13 +706,13 @@ template <bool MIXED, bool C64 = false>
 __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Stencils& st,
                                           const double* __restrict__ mp, const float* __restrict__ mp32,
                                           double* __restrict__ loc, unsigned char* smem) {
-  const HaloGeom gf = far_geom(st.radius);
+  const HaloGeom gf = far_geom(st.radius, MIXED);
   __shared__ int nleaf[27];
   const bool any_refined = load_leaf_neighbours(t, node, nleaf);
   float* halo32 = reinterpret_cast<float*>(smem);
   double* halo64 = reinterpret_cast<double*>(smem);
   if (MIXED)
-    stage_halo(gf, nleaf, mp, halo32);
+    stage_halo_mixed(gf, nleaf, mp32, halo32);
   else
     stage_halo(gf, nleaf, mp, halo64);
   __syncthreads();
@@ -679,15 +721,18 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
   const double ih = 1.0 / t.h[lvl], ih2 = ih * ih;
   double L0[2], L1[2][3];  // the thread's two cells (see leaf_cell)
   if (MIXED) {
-    // warp w = parity class w; lane (i, j, k0) owns the cells with c / 2 = k0 and
-    // k0 + 2: both share every stencil entry (one table entry feeds two halo reads
-    // and eight fused multiply-adds).  The warp's stencil table streams through
-    // shared memory in blocks of kLeafBlock entries (halo offsets, then float32
-    // kernel rows; kLeafTableBlockBytes per block), each fetched by one bulk
-    // asynchronous copy (TMA) issued a block ahead into the other of two buffers,
-    // so the entries are read from shared memory instead of L2.
+    // warp w = parity class w; lane (i, j, kh) owns the cells of parity planes 2 kh
+    // and 2 kh + 1 (leaf_cell).  The warp's stencil is a list of z-columns (runs of
+    // entries d, d + 2 e_z, ... whose sources are consecutive planes of one parity
+    // block): along a column the lane's first cell reads masses M_0 .. M_{L-1} and
+    // its second cell M_1 .. M_L, so one shared-memory load serves both cells, and
+    // each entry is four paired float32 FMAs (both cells' L0, L1 from the duplicated
+    // mass and the entry's kernel row).  The table streams through shared memory in
+    // blocks (kLeafTableBlockBytes: column headers, then kernel rows), each fetched
+    // by one bulk asynchronous copy (TMA) issued a block ahead into the other of two
+    // buffers; each block is one float32 partial sum, merged into compensated sums.
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nblk = (n_far + kLeafBlock - 1) / kLeafBlock;
+    const int nblk = lvl == 0 ? st.root_blocks : st.far_blocks;
     const unsigned char* gtab = reinterpret_cast<const unsigned char*>(st.leaf_blocks) +
                                 ((lvl == 0 ? (size_t)8 * st.far_blocks + (size_t)w * st.root_blocks
                                            : (size_t)w * st.far_blocks) *
@@ -696,14 +741,14 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + leaf_halo_bytes(st, true) +
                                                 (size_t)kLeafWarps * 2 * kLeafTableBlockBytes) +
                     2 * w;
-    const int lane_f = (lane & 3) + gf.PY * ((lane >> 2) & 3) + gf.PZ * (lane >> 4);
-    const int dz = 2 * gf.PZ;
+    const int lane_f = (lane & 3) + gf.PY * ((lane >> 2) & 3) + gf.PZ * 2 * (lane >> 4);
+    const int PZ = gf.PZ;
     KF f[2][4];
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
       for (int k = 0; k < 4; ++k) f[q][k] = 0.0f;
-    if (lane == 0) {
+    if (lane == 0 && nblk > 0) {
       tma::mbar_init(bar);
       tma::mbar_init(bar + 1);
       tma::fence_mbar_init();
@@ -723,33 +768,42 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
       }
       ok = __all_sync(0xffffffffu, tma::mbar_wait(bar + (b & 1), (b >> 1) & 1));
       if (!ok) break;
-      const int* offs = reinterpret_cast<const int*>(sbuf + (b & 1) * kLeafTableBlockBytes);
-      const float4* ks = reinterpret_cast<const float4*>(offs + kLeafBlock);
-      // one stencil entry: the two cells' masses times the entry's kernel row
-      auto entry = [&](int u, float* pa, float* pb) {
-        const int off = offs[u];
-        const float4 k = ks[u];
-        const float m0 = halo32[lane_f + off], m1 = halo32[lane_f + off + dz];
-        pa[0] = fmaf(m0, k.x, pa[0]);
-        pa[1] = fmaf(m0, k.y, pa[1]);
-        pa[2] = fmaf(m0, k.z, pa[2]);
-        pa[3] = fmaf(m0, k.w, pa[3]);
-        pb[0] = fmaf(m1, k.x, pb[0]);
-        pb[1] = fmaf(m1, k.y, pb[1]);
-        pb[2] = fmaf(m1, k.z, pb[2]);
-        pb[3] = fmaf(m1, k.w, pb[3]);
+      const int* hdr = reinterpret_cast<const int*>(sbuf + (b & 1) * kLeafTableBlockBytes);
+      const float4* ks = reinterpret_cast<const float4*>(hdr + kLeafBlock);
+      // (L0, L1x), (L1y, L1z) of cells A and B; two sets, even and odd chunks, for
+      // two independent FMA chains per sum
+      F2 acc[2][4] = {{bc(0.0f), bc(0.0f), bc(0.0f), bc(0.0f)}, {bc(0.0f), bc(0.0f), bc(0.0f), bc(0.0f)}};
+      // chunks of C entries, fully unrolled: the chunk's C + 1 masses (cell A reads
+      // M_0 .. M_{C-1}, cell B M_1 .. M_C), then four paired FMAs per entry
+      auto chunks = [&](auto c_, auto n_) {
+        constexpr int C = decltype(c_)::value, N = decltype(n_)::value;
+#pragma unroll
+        for (int ci = 0; ci < N; ++ci) {
+          const float* src = halo32 + lane_f + (hdr[ci] & 0xfffff);
+          F2 M[C + 1];
+#pragma unroll
+          for (int u = 0; u <= C; ++u) M[u] = bc(src[u * PZ]);
+          F2* a = acc[ci & 1];
+#pragma unroll
+          for (int u = 0; u < C; ++u) {
+            const float4 k = ks[C * ci + u];
+            const F2 k01 = f2(k.x, k.y), k23 = f2(k.z, k.w);
+            a[0] = fma2(M[u], k01, a[0]);
+            a[1] = fma2(M[u], k23, a[1]);
+            a[2] = fma2(M[u + 1], k01, a[2]);
+            a[3] = fma2(M[u + 1], k23, a[3]);
+          }
+        }
       };
-      float pa[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      const int n_in = min(kLeafBlock, n_far - b * kLeafBlock);
-      if (n_in == kLeafBlock) {  // full block fully unrolled (constant offsets, no loop control)
-#pragma unroll
-        for (int u = 0; u < kLeafBlock; ++u) entry(u, pa, pb);
-      } else {
-#pragma unroll 4
-        for (int u = 0; u < n_in; ++u) entry(u, pa, pb);
+      switch (hdr[0] >> 20) {  // warp-uniform chunk length of this block (0: empty)
+        case 3: chunks(std::integral_constant<int, 3>(), std::integral_constant<int, 10>()); break;
+        case 2: chunks(std::integral_constant<int, 2>(), std::integral_constant<int, 16>()); break;
+        case 1: chunks(std::integral_constant<int, 1>(), std::integral_constant<int, 32>()); break;
       }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) f[0][k].add(pa[k]), f[1][k].add(pb[k]);
+      const F2 A01 = acc[0][0] + acc[1][0], A23 = acc[0][1] + acc[1][1];
+      const F2 B01 = acc[0][2] + acc[1][2], B23 = acc[0][3] + acc[1][3];
+      f[0][0].add(A01.v.x), f[0][1].add(A01.v.y), f[0][2].add(A23.v.x), f[0][3].add(A23.v.y);
+      f[1][0].add(B01.v.x), f[1][1].add(B01.v.y), f[1][2].add(B23.v.x), f[1][3].add(B23.v.y);
       __syncwarp();  // every lane has read this buffer before it is refilled
     }
     if (!ok) {
@@ -763,7 +817,7 @@ __device__ __forceinline__ void leaf_item(const DevTree& t, int node, const Sten
     // leaf item of this block can initialise them again and other items may reuse
     // the memory
     __syncwarp();
-    if (lane == 0) {
+    if (lane == 0 && nblk > 0) {
       tma::mbar_inval(bar);
       tma::mbar_inval(bar + 1);
     }

@@ -15,10 +15,15 @@ struct alignas(16) Kappa {
   double v[4];
 };
 
-// Stencil entries per float32 partial sum of the leaf far field (a fully unrolled
-// block), and the bytes of one block of the mixed path's leaf table: kLeafBlock
-// int32 halo offsets, then kLeafBlock float4 kernel rows (a multiple of 16 bytes,
-// one bulk asynchronous copy).
+// The mixed path's leaf far-field tables are z-columns of a parity stencil (runs
+// of entries d, d + 2 e_z, d + 4 e_z, ...: consecutive planes of one parity block
+// of the halo) cut into chunks of 3, 2 or 1 entries.  A block of the table (one
+// bulk asynchronous copy, kLeafTableBlockBytes) holds chunks of one length C only:
+// kLeafBlock int32 chunk headers (halo offset of the chunk's first entry | C << 20;
+// a header of 0 ends the block), then kLeafBlock float4 kernel rows, chunk c at
+// rows C c .. C c + C - 1.  Blocks of C = 3 hold 10 chunks, C = 2 16, C = 1 32;
+// a partial block is padded with chunks of halo offset 0 and zero rows.  A block is
+// also one float32 partial sum.
 constexpr int kLeafBlock = 32;
 constexpr int kLeafTableBlockBytes = kLeafBlock * (4 + 16);
 
@@ -75,6 +80,14 @@ int build_pair_tables(const int* tab, int n, bool per_parity, std::vector<int32_
 // x-pairs of source cells as in build_pair_tables, for the x-parity of cell l.
 void build_cell_pair_lists(const std::vector<int32_t>& ent, const std::vector<int32_t>& off,
                            std::vector<int32_t>& pair_ent, std::vector<int32_t>& pair_off);
+
+// Host: the mixed path's leaf far-field table blocks (see kLeafBlock) of the stencil
+// tab (n packed offsets; per_parity: [8][n], else one table for every class) for a
+// far halo of border R, kernel rows from kap (the dense table over [-R, R]^3),
+// appended to out as [8][blocks] blocks of kLeafTableBlockBytes; returns the blocks
+// per parity class (every class padded to the most with empty blocks).
+int build_leaf_column_blocks(const int* tab, int n, bool per_parity, int R, const Kappa* kap,
+                             std::vector<uint4>& out);
 
 // Host: the leaf-item tables above for the given stencils and precision mode.
 void build_leaf_tables(const int* parity, int n_st, const int* root, int n_root, const int* near_, int n_near, int R,

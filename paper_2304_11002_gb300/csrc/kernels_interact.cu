@@ -9,6 +9,9 @@
 //    others.  The counter is reset by a memset issued before every launch; no block
 //    ever waits for another.
 // The autotuner in capi.cu times both on the actual tree and keeps the faster.
+#include <cstring>
+#include <set>
+
 #include "interact.cuh"
 
 namespace octo {
@@ -36,7 +39,7 @@ __global__ void __launch_bounds__(items::kThreads) k_near_items(DevTree t, const
 
 void build_leaf_tables(const int* parity, int n_st, const int* root, int n_root, const int* near_, int n_near, int R,
                        int RN, bool mixed, int2* far_out, int2* root_out, int2* near_out) {
-  const items::HaloGeom gf = items::far_geom(R), gn = mixed ? items::near_geom(RN) : items::far_geom(R);
+  const items::HaloGeom gf = items::far_geom(R, false), gn = mixed ? items::near_geom(RN) : items::far_geom(R, false);
   const int W = 2 * R + 1, kbase = R + W * R + W * W * R;
   // entry of offset d for targets of parity (pa, pb, pc) in a halo of border g.r
   auto entry = [&](const items::HaloGeom& g, int pa, int pb, int pc, int e) {
@@ -99,6 +102,65 @@ void build_cell_pair_lists(const std::vector<int32_t>& ent, const std::vector<in
     group_pairs(ent.data() + off[i], off[i + 1] - off[i], (l & 7) & 1, pair_ent);
     pair_off.push_back((int32_t)pair_ent.size());
   }
+}
+
+int build_leaf_column_blocks(const int* tab, int n, bool per_parity, int R, const Kappa* kap,
+                             std::vector<uint4>& out) {
+  const items::HaloGeom gf = items::far_geom(R, true);
+  const int W = 2 * R + 1, kbase = R + W * R + W * W * R;
+  struct Chunk {
+    int off, dx, dy, dz;  // halo offset and stencil offset of the first entry
+  };
+  constexpr int kPerBlock[4] = {0, 32, 16, 10};  // chunks per block of chunk length C
+  std::vector<std::vector<std::pair<int, std::vector<Chunk>>>> blocks(8);  // [p] -> (C, chunks)
+  size_t nb = 0;
+  for (int p = 0; p < 8; ++p) {
+    const int pa = p & 1, pb = (p >> 1) & 1, pc = p >> 2;
+    const int* tp = per_parity ? tab + (size_t)p * n : tab;
+    std::set<int32_t> in(tp, tp + n);
+    auto key = [](int dx, int dy, int dz) {
+      return (int32_t)(((uint32_t)(dx & 0xff)) | ((uint32_t)(dy & 0xff) << 8) | ((uint32_t)(dz & 0xff) << 16));
+    };
+    std::vector<Chunk> by_len[4];
+    for (int s = 0; s < n; ++s) {  // columns in the order of their first entry
+      const int e = tp[s];
+      const int dx = (int)(int8_t)(e & 0xff), dy = (int)(int8_t)((e >> 8) & 0xff), dz = (int)(int8_t)((e >> 16) & 0xff);
+      if (in.count(key(dx, dy, dz - 2))) continue;  // not the first entry of its column
+      int len = 0;
+      while (in.count(key(dx, dy, dz + 2 * len))) ++len;
+      // chunks of 3, then 2 + 2 for a remainder of 4 and 2 for a remainder of 2
+      for (int w = 0; w < len;) {
+        const int left = len - w, c = left == 1 ? 1 : left == 2 || left == 4 ? 2 : 3;
+        by_len[c].push_back({items::halo_index(gf, pa + R + dx, pb + R + dy, pc + R + dz + 2 * w), dx, dy, dz + 2 * w});
+        w += c;
+      }
+    }
+    for (int c = 3; c >= 1; --c)
+      for (size_t k = 0; k < by_len[c].size(); k += kPerBlock[c])
+        blocks[p].push_back({c, std::vector<Chunk>(by_len[c].begin() + k,
+                                                   by_len[c].begin() + std::min(by_len[c].size(), k + kPerBlock[c]))});
+    nb = std::max(nb, blocks[p].size());
+  }
+  constexpr int kWords = kLeafTableBlockBytes / 16;
+  const size_t b0 = out.size();
+  out.resize(b0 + (size_t)8 * nb * kWords, make_uint4(0, 0, 0, 0));
+  for (int p = 0; p < 8; ++p)
+    for (size_t bk = 0; bk < blocks[p].size(); ++bk) {
+      unsigned char* base = reinterpret_cast<unsigned char*>(&out[b0 + ((size_t)p * nb + bk) * kWords]);
+      const int C = blocks[p][bk].first;
+      const std::vector<Chunk>& ch = blocks[p][bk].second;
+      for (int ci = 0; ci < kPerBlock[C]; ++ci) {  // padding chunks: offset 0, zero rows
+        const int32_t h = (ci < (int)ch.size() ? ch[ci].off : 0) | (C << 20);
+        std::memcpy(base + 4 * ci, &h, 4);
+        if (ci >= (int)ch.size()) continue;
+        for (int w = 0; w < C; ++w) {
+          const Kappa& v = kap[kbase + ch[ci].dx + W * ch[ci].dy + W * W * (ch[ci].dz + 2 * w)];
+          const float k4[4] = {(float)v.v[0], (float)v.v[1], (float)v.v[2], (float)v.v[3]};
+          std::memcpy(base + 4 * kLeafBlock + 16 * (C * ci + w), k4, 16);
+        }
+      }
+    }
+  return (int)nb;
 }
 
 cudaError_t configure_interact_kernels() {
