@@ -132,8 +132,9 @@ def dist_env():
 # capture was taken with (sha256 over these files without their // comments and
 # blank lines), else null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-KERNEL_SOURCES = ("capi.cu", "cross.cuh", "device.cuh", "interact.cuh", "items.cuh", "kernels.h",
-                  "kernels_boundary.cu", "kernels_interact.cu", "kernels_interact_b64.cu", "pair_x2.cuh", "tma.cuh")
+KERNEL_SOURCES = ("capi.cu", "cross.cuh", "device.cuh", "halo.h", "interact.cuh", "items.cuh", "kernels.h",
+                  "kernels_boundary.cu", "kernels_interact.cu", "kernels_interact_b64.cu", "pair_x2.cuh", "tables.cpp",
+                  "tables.h", "tma.cuh")
 
 
 def code_lines(text: str):

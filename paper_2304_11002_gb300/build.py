@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "_lib", "liboctofmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["capi.cu", "kernels_fp64.cu", "kernels_adjoint.cu", "kernels_boundary.cu", "noalloc.cu",
               "kernels_interact.cu", "kernels_interact_b64.cu", "peak.cu", "scf.cu"]
-CXX_SOURCES = ["plan.cpp"]
+CXX_SOURCES = ["plan.cpp", "tables.cpp"]
 
 
 def nvcc() -> str:

@@ -808,9 +808,11 @@ int octo_fmm_create(const octo_tree_desc* tree, double theta, int order, int pre
     if (e == cudaSuccess) e = upload(&h->d_leaf_near, ln);
     if (precision == OCTO_MIXED) {
       // z-column blocks (see kLeafBlock): parity stencils, then level 0
-      std::vector<uint4> blk;
-      far_blocks = build_leaf_column_blocks(P.st_parity.data(), ns, true, R, kap.data(), blk);
-      root_blocks = build_leaf_column_blocks(P.st_root.data(), nr, false, R, kap.data(), blk);
+      std::vector<uint32_t> words;
+      far_blocks = build_leaf_column_blocks(P.st_parity.data(), ns, true, R, kap.data(), words);
+      root_blocks = build_leaf_column_blocks(P.st_root.data(), nr, false, R, kap.data(), words);
+      std::vector<uint4> blk(words.size() / 4);
+      std::memcpy(blk.data(), words.data(), sizeof(uint32_t) * words.size());
       if (e == cudaSuccess) e = upload(&h->d_leaf_blocks, blk);
     }
     if (e != cudaSuccess) {
