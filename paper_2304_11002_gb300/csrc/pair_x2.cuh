@@ -3,8 +3,12 @@
 // of two source cells, one per lane, and one instruction computes both lanes, each
 // rounded as its scalar counterpart.  The interior M2L is bound by instruction
 // issue, not by the float32 pipe, so computing two sources per instruction moves
-// its bound from issue to the pipe.  Device code only.
+// its bound from issue to the pipe.  Compiled as host code (no GPU) the same
+// functions compute each lane with the scalar float32 operation (the same
+// rounding), so that a host test can check the expression.
 #pragma once
+#include <cmath>
+
 #include "device.cuh"
 
 namespace octo {
@@ -13,8 +17,9 @@ struct F2 {
   float2 v;
 };
 
-__device__ __forceinline__ F2 f2(float x, float y) { return F2{make_float2(x, y)}; }
-__device__ __forceinline__ F2 bc(float s) { return F2{make_float2(s, s)}; }
+__host__ __device__ __forceinline__ F2 f2(float x, float y) { return F2{make_float2(x, y)}; }
+__host__ __device__ __forceinline__ F2 bc(float s) { return F2{make_float2(s, s)}; }
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
 __device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
 __device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
 __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
@@ -24,24 +29,35 @@ __device__ __forceinline__ F2 operator-(F2 a, F2 b) {
       "l"(*reinterpret_cast<unsigned long long*>(&b.v)));
   return F2{*reinterpret_cast<float2*>(&r)};
 }
+#else  // host code (and device code for architectures without the paired instructions)
+__host__ __device__ inline F2 operator+(F2 a, F2 b) { return f2(a.v.x + b.v.x, a.v.y + b.v.y); }
+__host__ __device__ inline F2 operator*(F2 a, F2 b) { return f2(a.v.x * b.v.x, a.v.y * b.v.y); }
+__host__ __device__ inline F2 fma2(F2 a, F2 b, F2 c) { return f2(fmaf(a.v.x, b.v.x, c.v.x), fmaf(a.v.y, b.v.y, c.v.y)); }
+__host__ __device__ inline F2 operator-(F2 a, F2 b) { return f2(a.v.x - b.v.x, a.v.y - b.v.y); }
+#endif
 
 // acc += x.x * y.x + x.y * y.y (two float32 FMAs); acc -= likewise; acc -= x.x + x.y.
-__device__ __forceinline__ void acc_fma(float& acc, F2 x, F2 y) {
+__host__ __device__ __forceinline__ void acc_fma(float& acc, F2 x, F2 y) {
   acc = fmaf(x.v.x, y.v.x, acc);
   acc = fmaf(x.v.y, y.v.y, acc);
 }
-__device__ __forceinline__ void acc_fms(float& acc, F2 x, F2 y) {
+__host__ __device__ __forceinline__ void acc_fms(float& acc, F2 x, F2 y) {
   acc = fmaf(-x.v.x, y.v.x, acc);
   acc = fmaf(-x.v.y, y.v.y, acc);
 }
-__device__ __forceinline__ void acc_sub(float& acc, F2 x) {
+__host__ __device__ __forceinline__ void acc_sub(float& acc, F2 x) {
   acc -= x.v.x;
   acc -= x.v.y;
 }
 
-// 1/sqrt(x) per lane: the hardware estimate and one Newton step (rsqrt_f32).
-__device__ __forceinline__ F2 rsqrt2(F2 x) {
+// 1/sqrt(x) per lane: the hardware estimate (host: 1 / sqrt) and one Newton step
+// (rsqrt_f32).
+__host__ __device__ __forceinline__ F2 rsqrt2(F2 x) {
+#ifdef __CUDA_ARCH__
   const F2 y = f2(rsqrtf(x.v.x), rsqrtf(x.v.y));
+#else
+  const F2 y = f2(1.0f / std::sqrt(x.v.x), 1.0f / std::sqrt(x.v.y));
+#endif
   const F2 e = fma2(bc(-1.0f) * x * y, y, bc(1.0f));
   return fma2(y * bc(0.5f), e, y);
 }
@@ -56,7 +72,7 @@ __device__ __forceinline__ F2 rsqrt2(F2 x) {
 // LeafAcc<float>; no target octupole, Oh and tOh unused).  A lane whose m, Q and O
 // are zero contributes exactly zero.
 template <bool INTERIOR, typename A>
-__device__ __forceinline__ void m2l_pair_x2(const F2 R0, const F2 R1, const F2 R2, const F2 m, const F2* Q,
+__host__ __device__ __forceinline__ void m2l_pair_x2(const F2 R0, const F2 R1, const F2 R2, const F2 m, const F2* Q,
                                             const F2* O, const float* Oh, const float* tOh, const F2 rinv, A& a) {
   const F2 ir2 = rinv * rinv;
   const F2 f0 = rinv;

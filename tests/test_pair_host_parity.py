@@ -72,3 +72,28 @@ def test_float32_pair_expression_within_float32_rounding(tmp_path):
     err = np.max(np.abs(got - want), axis=0) / np.max(np.abs(want), axis=0)
     assert np.all(err <= 32 * 2.0**-24), err
     assert np.max(err) > 1e-12  # it did run in float32
+
+
+@pytest.mark.parametrize("mode", ["lane0", "lane1", "both", "leaf"])
+def test_paired_float32_expression(tmp_path, mode):
+    """The paired float32 expression of the mixed far field (m2l_pair_x2,
+    pair_x2.cuh; on the host each lane is the scalar float32 operation) against
+    the oracle's pair M2L: a source in either lane with the other lane masked to
+    zero mass and moments gives that pair, the same source in both lanes twice the
+    pair, and the leaf-target form the leaf components (L0, L1 and the correction
+    without a target octupole); all within 32 float32 rounding units of the
+    largest value of every component."""
+    leaf = mode == "leaf"
+    rng = np.random.default_rng(23 + ["lane0", "lane1", "both", "leaf"].index(mode))
+    A, B = _records(rng, 64, leaf)
+    flag = {"lane0": 3, "lane1": 4, "both": 5, "leaf": 6}[mode]
+    got = _evaluate(tmp_path, flag, A, B)
+    want = np.array([oracle.m2l_pair(a, b, correction=True) for a, b in zip(A, B)])
+    if mode == "both":
+        want = 2.0 * want
+    cols = np.r_[0:4, 20:23] if leaf else np.arange(23)
+    err = np.max(np.abs(got[:, cols] - want[:, cols]), axis=0) / np.max(np.abs(want[:, cols]), axis=0)
+    assert np.all(err <= 32 * 2.0**-24), err
+    assert np.max(err) > 1e-12  # it did run in float32
+    if leaf:
+        assert np.all(got[:, 4:20] == 0.0)
