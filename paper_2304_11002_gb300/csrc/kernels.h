@@ -26,10 +26,10 @@ struct Stencils {
   const int* near_;   // non-zero near offsets
   int n_near;
   const Kappa* kappa;    // dense monopole kernel table over [-R, R]^3, unit cell width
-  const uint4* leaf_blocks;  // mixed path: the leaf far-field tables in blocks of 32 entries
-                             // (32 int32 halo offsets, then 32 float4 kernel rows, 640
-                             // bytes; zero-padded): [8][far_blocks] for the parity
-                             // stencils, then [8][root_blocks] for the level-0 stencil
+  const uint4* leaf_blocks;  // mixed path: the leaf far-field tables as blocks of z-column
+                             // chunks (see kLeafBlock in tables.h; 640 bytes each):
+                             // [8][far_blocks] for the parity stencils, then
+                             // [8][root_blocks] for the level-0 stencil
   int far_blocks, root_blocks;
   int radius;            // R: maximum |offset component|
   int near_radius;       // maximum |offset component| of the near offsets
